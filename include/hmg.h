@@ -1,0 +1,194 @@
+/*
+ * hmg.h -- C ABI of the GB300 tensor-product multigrid solver for the lumped
+ * pressure-Helmholtz operator of the lowest-order (RT0 x DG0) mixed finite
+ * element discretisation on an extruded icosahedral shell.
+ *
+ * Method: Mitchell & Mueller, "High level implementation of geometric
+ * multigrid solvers for finite element problems: applications in atmospheric
+ * modelling".  The operator is H^ of Sec. 4.2, Eq. (Preconditioner); the
+ * preconditioner is the horizontal-only V-cycle of Sec. 4.2.1 (vertical line
+ * relaxation, Eq. (BlockJacobi) in the form of Sec. 5.4, DG0 transfers of
+ * Sec. 3.2, Algorithm 1), wrapped in a Krylov solve (Sec. 5).
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Every function returns an hmg_status; none aborts or exits.
+ * - Device pointers are CUDA device (or managed) memory owned by the caller
+ *   unless stated otherwise; host pointers are ordinary host memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   All GPU work is enqueued on it.  Argument errors are reported
+ *   synchronously; errors raised by kernels are reported by the next call
+ *   that synchronises (hmg_solve, hmg_solve_host) or by hmg_sync.
+ * - Vectors are FP64 (or FP32 where a dtype argument says so) over the cells
+ *   of one level.  Layout HMG_LAYOUT_COLUMN numbers cell (column c, layer l)
+ *   as c * nlayers + l, all unknowns of a column consecutive (Sec. 4.3).
+ *   Layout HMG_LAYOUT_TILED is the library's working layout: columns in
+ *   tiles of 32, layer-major inside a tile,
+ *       index = (c / 32) * 32 * nlayers + l * 32 + (c % 32),
+ *   over ncols_padded = 32 * ceil(ncols / 32) columns; padding entries are
+ *   written as zero and must be zero on input.
+ * - Level 0 is the finest mesh; level k has 20 * 4^(refinement - k) columns
+ *   and the parent of column c on level k is column c / 4 on level k + 1.
+ * - A context is not thread safe; calls on one context must be ordered.
+ */
+#ifndef HMG_H
+#define HMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMG_OK = 0,
+  HMG_ERR_INVALID_ARG = 1,   /* bad pointer, size, level or parameter */
+  HMG_ERR_CUDA = 2,          /* a CUDA runtime call or kernel failed */
+  HMG_ERR_OOM = 3,           /* device or host allocation failed */
+  HMG_ERR_NOT_CONVERGED = 4, /* max_iter reached; info is filled in */
+  HMG_ERR_BREAKDOWN = 5,     /* Krylov breakdown (p.q <= 0 or r.z <= 0) */
+  HMG_ERR_NONFINITE = 6,     /* NaN or Inf in the right-hand side or residual */
+  HMG_ERR_STATE = 7          /* call out of order (e.g. solve before assemble) */
+} hmg_status;
+
+typedef enum { HMG_FP64 = 0, HMG_FP32 = 1 } hmg_dtype;
+typedef enum { HMG_LAYOUT_COLUMN = 0, HMG_LAYOUT_TILED = 1 } hmg_layout;
+typedef enum { HMG_PRECISION_FP64 = 0, HMG_PRECISION_MIXED = 1 } hmg_precision;
+typedef enum { HMG_KRYLOV_CG = 0, HMG_KRYLOV_FCG = 1 } hmg_krylov;
+
+/* Shell and hierarchy (Sec. 3.1, Sec. 4.1, Table "Grid setup"). */
+typedef struct {
+  int refinement;       /* finest icosahedral refinement r >= 0 (20 * 4^r columns) */
+  int nlayers;          /* vertical layers, 1 <= nlayers <= 1024 */
+  int nlevels;          /* multigrid levels, 1 <= nlevels <= refinement + 1 */
+  double radius_m;      /* inner radius R of the shell, > 0 (6.371e6) */
+  double thickness_m;   /* shell thickness H, > 0 (1.0e4) */
+} hmg_mesh_params;
+
+/* Operator parameters (Sec. 4.1, Eq. HelmholtzOperator, Eq.
+ * PressureVelocitySystem, Sec. 5).  dt = nu_cfl * dx_m / c, w_c = c dt / 2,
+ * w_N = N dt / 2.  dx_m <= 0 selects 90 km * 2^(6 - refinement). */
+typedef struct {
+  double c;             /* speed of sound, m/s (300) */
+  double N;             /* buoyancy frequency, 1/s (0.01), >= 0 */
+  double nu_cfl;        /* horizontal acoustic Courant number (8) */
+  double dx_m;          /* horizontal grid spacing defining dt; <= 0: default */
+  double omega;         /* smoother over-relaxation, 0 < omega < 2 (0.8) */
+} hmg_op_params;
+
+typedef struct {
+  int precision;        /* hmg_precision */
+  int krylov;           /* hmg_krylov; MIXED always runs flexible CG */
+  double rtol;          /* stop when ||r_k||_2 / ||b||_2 < rtol (1e-8) */
+  int max_iter;         /* >= 1 */
+  int nu_pre;           /* pre-smoothing sweeps per level, >= 1 (2) */
+  int nu_post;          /* post-smoothing sweeps per level, >= 1 (2) */
+  int n_coarse;         /* smoother iterations on the coarsest level, >= 1 (2) */
+} hmg_solve_params;
+
+typedef struct {
+  int iterations;           /* Krylov iterations performed */
+  int converged;            /* 1 if ||r||/||b|| < rtol */
+  double rel_residual;      /* recursive residual ||r_k|| / ||b|| */
+  double true_rel_residual; /* ||b - H^ x|| / ||b||, recomputed at the end */
+  double solve_ms;          /* device time of the solve (CUDA events) */
+} hmg_solve_info;
+
+typedef struct {
+  int refinement;       /* icosahedral refinement of this level */
+  int ncols;            /* columns 20 * 4^refinement */
+  int ncols_padded;     /* ncols rounded up to a multiple of 32 */
+  int nlayers;
+  int64_t ncells;       /* ncols * nlayers (COLUMN layout length) */
+  int64_t ncells_padded;/* ncols_padded * nlayers (TILED layout length) */
+} hmg_level_info;
+
+typedef struct hmg_ctx hmg_ctx;
+
+/* Build the mesh hierarchy (Sec. 3.1): the icosahedron refined `refinement`
+ * times by edge bisection with midpoints projected to the sphere, children of
+ * column c at 4c..4c+3, three neighbours per column, radial extrusion into
+ * `nlayers` uniform layers (Sec. 4.1).  Allocates all device memory of the
+ * hierarchy on the current device.  *out receives a new context, owned by the
+ * caller and released with hmg_destroy.  Errors: INVALID_ARG, OOM, CUDA. */
+hmg_status hmg_build_hierarchy(const hmg_mesh_params* params, hmg_ctx** out);
+
+/* Release every resource of a context (NULL is accepted). */
+hmg_status hmg_destroy(hmg_ctx* ctx);
+
+hmg_status hmg_get_level_info(const hmg_ctx* ctx, int level, hmg_level_info* out);
+
+/* Copy one level's mesh to caller-owned host buffers (any may be NULL):
+ * centroids[3 * ncols] = flat-triangle centroids on the unit sphere,
+ * nbr[3 * ncols] = column across the edge opposite vertex k of each column.
+ * Used to match cells with an independent implementation. */
+hmg_status hmg_export_mesh(const hmg_ctx* ctx, int level, double* centroids, int32_t* nbr);
+
+/* Assemble H^ and H^_z on every level (Sec. 4.2, Eq. Preconditioner and
+ * Eq. HHgeneralbanded; coarse levels rediscretised, Sec. 3.3) and factorise
+ * H^_z = L D L^T per column for the Thomas solve (Sec. 4.3.1).  Builds FP64
+ * and FP32 copies of all coefficients.
+ * theta: NULL, or a device FP64 vector (COLUMN layout, finest level) of
+ * positive coefficients dividing each cell's share of the vertical lumped
+ * mass; coarse levels use the mean over the four children.  The values are
+ * copied; the pointer is read during this call only.
+ * Errors: INVALID_ARG (bad parameters), STATE (no hierarchy), CUDA. */
+hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* params,
+                                  const double* theta, void* stream);
+
+/* y = H^ x on `level` (Sec. 5.4, "operator application").  x and y are
+ * device vectors of type `dtype` in `layout`; x != y.  FP32 uses the FP32
+ * copy of the coefficients.  Errors: INVALID_ARG, STATE, CUDA. */
+hmg_status hmg_apply(hmg_ctx* ctx, int level, int dtype, int layout,
+                     const void* x, void* y, void* stream);
+
+/* z = V r: one V-cycle from a zero initial guess on the finest level
+ * (Algorithm 1 applied recursively; line relaxation of Sec. 4.2.1 with
+ * nu_pre / nu_post sweeps per level and n_coarse sweeps on the coarsest
+ * level).  r and z are FP64 device vectors in `layout`; precision
+ * HMG_PRECISION_MIXED runs levels 0..nlevels-2 in FP32 and the coarsest level
+ * in FP64.  r != z.  Errors: INVALID_ARG, STATE, CUDA. */
+hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r,
+                      void* z, int nu_pre, int nu_post, int n_coarse, void* stream);
+
+/* Solve H^ x = b on the finest level with CG (or flexible CG) preconditioned
+ * by one V-cycle per iteration, x_0 = 0 (Sec. 5; CG because H^ is symmetric
+ * positive definite).  b, x: FP64 device vectors, COLUMN layout, ncells.
+ * Blocks until the solve has finished.  Returns NOT_CONVERGED (info filled in)
+ * when max_iter is reached, NONFINITE for a non-finite b or residual,
+ * BREAKDOWN when p.q <= 0 or r.z <= 0. */
+hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x,
+                     const hmg_solve_params* params, hmg_solve_info* info, void* stream);
+
+/* hmg_solve with HOST buffers: copies b host->device, solves, copies x
+ * device->host, all on `stream`; page-locked buffers give asynchronous copies. */
+hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host,
+                          const hmg_solve_params* params, hmg_solve_info* info, void* stream);
+
+/* Adjoint face contraction: grad_theta_K = -lambda^T (dH^/dtheta_K) p for the
+ * theta given to the last hmg_assemble_helmholtz (all ones if NULL).  Only
+ * the vertical term of Eq. (Preconditioner) depends on theta, through the two
+ * vertical faces of K.  p, lambda, grad: FP64 device vectors, COLUMN layout,
+ * finest level.  Errors: INVALID_ARG, STATE, CUDA. */
+hmg_status hmg_theta_grad(hmg_ctx* ctx, const double* p, const double* lambda,
+                          double* grad, void* stream);
+
+/* Convert a finest-level (or any level) FP64 vector between layouts. */
+hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* src,
+                         int dst_layout, double* dst, void* stream);
+
+/* Synchronise `stream` and report any pending device error. */
+hmg_status hmg_sync(hmg_ctx* ctx, void* stream);
+
+/* Human-readable description of the last error on this context ("" if none),
+ * or of the last build failure when ctx is NULL.  Owned by the library. */
+const char* hmg_last_error(const hmg_ctx* ctx);
+
+const char* hmg_status_string(hmg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMG_H */

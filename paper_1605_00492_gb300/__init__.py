@@ -1,0 +1,246 @@
+"""GB300 tensor-product multigrid solver for the lumped pressure-Helmholtz
+operator of Mitchell & Mueller's LO (RT0 x DG0) discretisation on an
+extruded icosahedral shell.
+
+This module is argument marshalling only: every step of the path runs in the
+CUDA kernels of ``libhmg.so`` (``include/hmg.h``).  PyTorch supplies device
+memory and streams.  There is no CPU fallback: importing this package fails
+if the library is missing.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+HMG_OK = 0
+STATUS = {
+    0: "HMG_OK", 1: "HMG_ERR_INVALID_ARG", 2: "HMG_ERR_CUDA", 3: "HMG_ERR_OOM",
+    4: "HMG_ERR_NOT_CONVERGED", 5: "HMG_ERR_BREAKDOWN", 6: "HMG_ERR_NONFINITE", 7: "HMG_ERR_STATE",
+}
+FP64, FP32 = 0, 1
+LAYOUT = {"column": 0, "tiled": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+KRYLOV = {"cg": 0, "fcg": 1}
+
+
+class HMGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class MeshParams(ctypes.Structure):
+    _fields_ = [("refinement", ctypes.c_int), ("nlayers", ctypes.c_int), ("nlevels", ctypes.c_int),
+                ("radius_m", ctypes.c_double), ("thickness_m", ctypes.c_double)]
+
+
+class OpParams(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("N", ctypes.c_double), ("nu_cfl", ctypes.c_double),
+                ("dx_m", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("krylov", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("n_coarse", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LevelInfo(ctypes.Structure):
+    _fields_ = [("refinement", ctypes.c_int), ("ncols", ctypes.c_int), ("ncols_padded", ctypes.c_int),
+                ("nlayers", ctypes.c_int), ("ncells", ctypes.c_int64), ("ncells_padded", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGNATURES = {
+    "hmg_build_hierarchy": [ctypes.POINTER(MeshParams), ctypes.POINTER(_P)],
+    "hmg_destroy": [_P],
+    "hmg_get_level_info": [_P, _I, ctypes.POINTER(LevelInfo)],
+    "hmg_export_mesh": [_P, _I, _P, _P],
+    "hmg_assemble_helmholtz": [_P, ctypes.POINTER(OpParams), _P, _P],
+    "hmg_apply": [_P, _I, _I, _I, _P, _P, _P],
+    "hmg_vcycle": [_P, _I, _I, _P, _P, _I, _I, _I, _P],
+    "hmg_solve": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
+    "hmg_solve_host": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
+    "hmg_theta_grad": [_P, _P, _P, _P, _P],
+    "hmg_to_layout": [_P, _I, _I, _P, _I, _P, _P],
+    "hmg_sync": [_P, _P],
+    "hmg_last_error": [_P],
+    "hmg_status_string": [_I],
+}
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libhmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1605_00492_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name in ("hmg_last_error", "hmg_status_string") else ctypes.c_int
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Workload:
+    refinement: int
+    nlayers: int
+    nlevels: int
+
+
+class Hierarchy:
+    """Mesh hierarchy plus assembled operator on the current CUDA device."""
+
+    def __init__(self, refinement, nlayers, nlevels, radius_m=6.371e6, thickness_m=1.0e4):
+        self.lib = load_library()
+        self._ctx = _P()
+        p = MeshParams(refinement, nlayers, nlevels, radius_m, thickness_m)
+        st = self.lib.hmg_build_hierarchy(ctypes.byref(p), ctypes.byref(self._ctx))
+        if st != HMG_OK:
+            raise HMGError(st, self.lib.hmg_last_error(None).decode())
+        self.refinement, self.nlayers, self.nlevels = refinement, nlayers, nlevels
+        self.levels = [self.level_info(k) for k in range(nlevels)]
+        self.ncells = self.levels[0]["ncells"]
+
+    def _check(self, st, allow=()):
+        if st != HMG_OK and st not in allow:
+            raise HMGError(st, self.lib.hmg_last_error(self._ctx).decode())
+        return st
+
+    def close(self):
+        if self._ctx:
+            self.lib.hmg_destroy(self._ctx)
+            self._ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_info(self, level):
+        info = LevelInfo()
+        self._check(self.lib.hmg_get_level_info(self._ctx, level, ctypes.byref(info)))
+        return {k: getattr(info, k) for k, _ in info._fields_}
+
+    def export_mesh(self, level=0):
+        import numpy as np
+        nc = self.levels[level]["ncols"]
+        cen = np.zeros((nc, 3), dtype=np.float64)
+        nbr = np.zeros((nc, 3), dtype=np.int32)
+        self._check(self.lib.hmg_export_mesh(self._ctx, level, cen.ctypes.data_as(_P), nbr.ctypes.data_as(_P)))
+        return cen, nbr
+
+    def assemble(self, theta=None, c=300.0, N=0.01, nu_cfl=8.0, dx_m=0.0, omega=0.8, stream=None):
+        p = OpParams(c, N, nu_cfl, dx_m, omega)
+        th = None
+        if theta is not None:
+            th = theta.contiguous()
+            assert th.dtype == torch.float64 and th.is_cuda and th.numel() == self.ncells
+        self._check(self.lib.hmg_assemble_helmholtz(self._ctx, ctypes.byref(p), _ptr(th) if th is not None else None,
+                                                    _stream(stream)))
+        return self
+
+    def _len(self, level, layout):
+        return self.levels[level]["ncells" if layout == "column" else "ncells_padded"]
+
+    def apply(self, x, level=0, layout="column", out=None, stream=None):
+        dtype = FP64 if x.dtype == torch.float64 else FP32
+        assert x.is_cuda and x.numel() == self._len(level, layout)
+        x = x.contiguous()
+        y = out if out is not None else torch.empty_like(x)
+        self._check(self.lib.hmg_apply(self._ctx, level, dtype, LAYOUT[layout], _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def vcycle(self, r, precision="fp64", layout="column", nu_pre=2, nu_post=2, n_coarse=2, out=None, stream=None):
+        assert r.is_cuda and r.dtype == torch.float64 and r.numel() == self._len(0, layout)
+        r = r.contiguous()
+        z = out if out is not None else torch.empty_like(r)
+        self._check(self.lib.hmg_vcycle(self._ctx, PRECISION[precision], LAYOUT[layout], _ptr(r), _ptr(z),
+                                        nu_pre, nu_post, n_coarse, _stream(stream)))
+        return z
+
+    def solve_params(self, precision="fp64", krylov="cg", rtol=1e-8, max_iter=500, nu_pre=2, nu_post=2,
+                     n_coarse=2):
+        return SolveParams(PRECISION[precision], KRYLOV[krylov], rtol, max_iter, nu_pre, nu_post, n_coarse)
+
+    def solve(self, b, out=None, stream=None, raise_on_failure=True, **kw):
+        """x = H^^-1 b by preconditioned CG; returns (x, info dict)."""
+        assert b.is_cuda and b.dtype == torch.float64 and b.numel() == self.ncells
+        b = b.contiguous()
+        x = out if out is not None else torch.empty_like(b)
+        info = SolveInfo()
+        p = self.solve_params(**kw)
+        st = self.lib.hmg_solve(self._ctx, _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(info), _stream(stream))
+        d = info.as_dict()
+        d["status"] = STATUS.get(st, st)
+        if raise_on_failure:
+            self._check(st)
+        return x, d
+
+    def solve_host(self, b_host, x_host, stream=None, raise_on_failure=True, **kw):
+        """Solve with HOST tensors (pinned for asynchronous copies)."""
+        assert not b_host.is_cuda and b_host.dtype == torch.float64 and b_host.numel() == self.ncells
+        info = SolveInfo()
+        p = self.solve_params(**kw)
+        st = self.lib.hmg_solve_host(self._ctx, _ptr(b_host), _ptr(x_host), ctypes.byref(p), ctypes.byref(info),
+                                     _stream(stream))
+        d = info.as_dict()
+        d["status"] = STATUS.get(st, st)
+        if raise_on_failure:
+            self._check(st)
+        return x_host, d
+
+    def theta_grad(self, p, lam, out=None, stream=None):
+        g = out if out is not None else torch.empty_like(p)
+        self._check(self.lib.hmg_theta_grad(self._ctx, _ptr(p.contiguous()), _ptr(lam.contiguous()), _ptr(g),
+                                            _stream(stream)))
+        return g
+
+    def to_layout(self, v, src="column", dst="tiled", level=0, stream=None):
+        out = torch.zeros(self._len(level, dst), dtype=torch.float64, device=v.device)
+        self._check(self.lib.hmg_to_layout(self._ctx, level, LAYOUT[src], _ptr(v.contiguous()), LAYOUT[dst],
+                                           _ptr(out), _stream(stream)))
+        return out
+
+    def sync(self, stream=None):
+        self._check(self.lib.hmg_sync(self._ctx, _stream(stream)))
+
+
+from .autograd import HelmholtzSolve  # noqa: E402  (needs Hierarchy)
+
+__all__ = ["Hierarchy", "HelmholtzSolve", "HMGError", "load_library", "LIB_PATH"]

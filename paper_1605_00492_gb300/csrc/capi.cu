@@ -1,0 +1,598 @@
+// C ABI of the library (include/hmg.h): context life cycle, assembly driver,
+// V-cycle driver (Algorithm 1, recursive correction scheme) and the
+// preconditioned CG / flexible CG loop (Sec. 5).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+
+#include "hmg_internal.h"
+
+using namespace hmg;
+
+namespace {
+
+std::string g_build_error;
+
+struct Fail {
+  hmg_status st;
+  std::string msg;
+};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    throw Fail{HMG_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+  throw Fail{HMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void launched(const char* what) { cuda_ok(cudaGetLastError(), what); }
+
+template <typename T>
+T* dalloc(hmg_ctx* c, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cuda_ok(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+  c->allocations.push_back(p);
+  cuda_ok(cudaMemset(p, 0, count * sizeof(T)), "cudaMemset");
+  return static_cast<T*>(p);
+}
+
+void release(hmg_ctx* c) {
+  for (void* p : c->allocations) cudaFree(p);
+  c->allocations.clear();
+  if (c->host_sc) cudaFreeHost(c->host_sc);
+  c->host_sc = nullptr;
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  c->ev0 = c->ev1 = nullptr;
+}
+
+template <typename F>
+hmg_status guarded(hmg_ctx* c, F&& f) {
+  try {
+    f();
+    if (c) c->err.clear();
+    return HMG_OK;
+  } catch (const Fail& e) {
+    if (c) c->err = e.msg;
+    else g_build_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    else g_build_error = "host allocation failed";
+    return HMG_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    else g_build_error = e.what();
+    return HMG_ERR_INVALID_ARG;
+  }
+}
+
+void require(bool ok, const std::string& msg) {
+  if (!ok) throw Fail{HMG_ERR_INVALID_ARG, msg};
+}
+
+// ------------------------------------------------------------ V-cycle driver
+
+struct CycleCfg {
+  int nu_pre = 2, nu_post = 2, n_coarse = 2;
+  bool mixed = false;
+  double omega = 0.8;
+};
+
+int level_dt(const hmg_ctx* c, const CycleCfg& cfg, int lev) {
+  return (cfg.mixed && lev < (int)c->lv.size() - 1) ? HMG_FP32 : HMG_FP64;
+}
+
+void* work(Level& L, int dt, int which) {
+  if (dt == HMG_FP64) return which == 0 ? (void*)L.ua64 : (which == 1 ? (void*)L.ub64 : (void*)L.b64);
+  return which == 0 ? (void*)L.ua32 : (which == 1 ? (void*)L.ub32 : (void*)L.b32);
+}
+
+// out <- V_lev b (zero initial guess).  b has type b_dt, out has type out_dt;
+// out must not be one of the level's work buffers ua / ub.
+void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, void* out, int out_dt,
+           cudaStream_t s) {
+  Level& L = c->lv[lev];
+  const int nlev = (int)c->lv.size();
+  const int dt = level_dt(c, cfg, lev);
+  const bool coarsest = lev == nlev - 1;
+  const int npre = coarsest ? cfg.n_coarse : cfg.nu_pre;
+  void* A = work(L, dt, 0);
+  void* B = work(L, dt, 1);
+  float* bcopy = (dt == HMG_FP32 && b_dt == HMG_FP64) ? L.b32 : nullptr;
+
+  if (coarsest && npre == 1 && out_dt == dt && !bcopy) {
+    launch_sweep0(L, dt, b, b_dt, out, nullptr, cfg.omega, s);
+    launched("sweep0");
+    return;
+  }
+  launch_sweep0(L, dt, b, b_dt, A, bcopy, cfg.omega, s);
+  launched("sweep0");
+  const void* bl = bcopy ? (const void*)bcopy : b;
+  void* cur = A;
+  void* nxt = B;
+  for (int i = 1; i < npre; ++i) {
+    bool last = coarsest && i == npre - 1;
+    launch_sweep(L, dt, bl, cur, last ? out : nxt, last ? out_dt : dt, L.y32, nullptr, dt, cfg.omega, s);
+    launched("sweep");
+    if (last) return;
+    std::swap(cur, nxt);
+  }
+  if (coarsest)  // n_coarse == 1 with a result that changes buffer type: not produced by any caller
+    throw Fail{HMG_ERR_INVALID_ARG, "unsupported coarsest-level configuration"};
+  // residual, restricted to the next coarser level
+  Level& C = c->lv[lev + 1];
+  const int cdt = level_dt(c, cfg, lev + 1);
+  void* bc = work(C, cdt, 2);
+  launch_resid_restrict(L, dt, bl, cur, bc, cdt, s);
+  launched("resid_restrict");
+  void* ec = cdt == HMG_FP64 ? (void*)C.ux64 : (void*)C.ux32;
+  cycle(c, cfg, lev + 1, bc, cdt, ec, cdt, s);
+  // post-smoothing; the coarse correction is prolonged into the first sweep
+  // (FP32) or added by its own pass first (FP64: fewer FP64 operations).
+  const void* ec_in = ec;
+  if (dt == HMG_FP64) {
+    launch_prolong(L, dt, cur, ec, cdt, s);
+    launched("prolong");
+    ec_in = nullptr;
+  }
+  for (int i = 0; i < cfg.nu_post; ++i) {
+    bool last = i == cfg.nu_post - 1;
+    launch_sweep(L, dt, bl, cur, last ? out : nxt, last ? out_dt : dt, L.y32, i == 0 ? ec_in : nullptr, cdt,
+                 cfg.omega, s);
+    launched("sweep");
+    std::swap(cur, nxt);
+  }
+}
+
+void check_cycle_params(int nu_pre, int nu_post, int n_coarse) {
+  require(nu_pre >= 1 && nu_pre <= 64, "nu_pre must be in [1, 64]");
+  require(nu_post >= 1 && nu_post <= 64, "nu_post must be in [1, 64]");
+  require(n_coarse >= 1 && n_coarse <= 64, "n_coarse must be in [1, 64]");
+}
+
+// ------------------------------------------------------------ Krylov driver
+
+void read_scalars(hmg_ctx* c, cudaStream_t s) {
+  cuda_ok(cudaMemcpyAsync(c->host_sc, c->red.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s),
+          "scalar read");
+  cuda_ok(cudaStreamSynchronize(s), "solve");
+}
+
+Reduce red_with(const hmg_ctx* c, int epi, int slot = 0) {
+  Reduce r = c->red;
+  r.epilogue = epi;
+  r.slot = slot;
+  return r;
+}
+
+hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  Level& L = c->lv[0];
+  CycleCfg cfg;
+  cfg.nu_pre = p.nu_pre;
+  cfg.nu_post = p.nu_post;
+  cfg.n_coarse = p.n_coarse;
+  cfg.mixed = p.precision == HMG_PRECISION_MIXED;
+  cfg.omega = c->ph.omega;
+  const bool flexible = cfg.mixed || p.krylov == HMG_KRYLOV_FCG;
+  const size_t bytes = (size_t)L.Np * sizeof(double);
+  hmg_solve_info inf{};
+
+  cuda_ok(cudaEventRecord(c->ev0, s), "event");
+  cuda_ok(cudaMemsetAsync(c->red.sc, 0, S_COUNT * sizeof(double), s), "memset");
+  cuda_ok(cudaMemsetAsync(c->kx, 0, bytes, s), "memset");
+  cuda_ok(cudaMemcpyAsync(c->kr, c->kb, bytes, cudaMemcpyDeviceToDevice, s), "copy");
+  launch_dot(L, c->kr, c->kr, nullptr, nullptr, red_with(c, EPI_STORE0, S_BB), s);
+  launched("dot");
+  read_scalars(c, s);
+  const double bb = c->host_sc[S_BB];
+  if (((int)c->host_sc[S_FLAG] & F_NONFINITE) || !std::isfinite(bb)) {
+    if (info) *info = inf;
+    throw Fail{HMG_ERR_NONFINITE, "right-hand side is not finite"};
+  }
+  hmg_status st = HMG_ERR_NOT_CONVERGED;
+  if (bb == 0.0) {
+    inf.converged = 1;
+    st = HMG_OK;
+  } else {
+    cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
+    launch_dot(L, c->kr, c->kz, nullptr, nullptr, red_with(c, EPI_INIT_RZ), s);
+    launched("dot");
+    cuda_ok(cudaMemcpyAsync(c->kp, c->kz, bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    const double stop2 = p.rtol * p.rtol * bb;
+    for (int k = 1; k <= p.max_iter; ++k) {
+      Reduce ra = red_with(c, EPI_ALPHA);
+      launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s);
+      launched("apply");
+      launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s);
+      launched("update_xr");
+      read_scalars(c, s);
+      inf.iterations = k;
+      int flag = (int)c->host_sc[S_FLAG];
+      double rr = c->host_sc[S_RR];
+      inf.rel_residual = std::sqrt(rr / bb);
+      if (flag & F_NONFINITE) {
+        st = HMG_ERR_NONFINITE;
+        break;
+      }
+      if (flag & F_BREAKDOWN) {
+        st = HMG_ERR_BREAKDOWN;
+        break;
+      }
+      if (rr < stop2) {
+        inf.converged = 1;
+        st = HMG_OK;
+        break;
+      }
+      if (k == p.max_iter) break;
+      cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
+      launch_dot(L, c->kr, c->kz, flexible ? c->kz : nullptr, c->kq,
+                 red_with(c, flexible ? EPI_BETA_FCG : EPI_BETA_CG), s);
+      launched("dot");
+      launch_update_p(L, c->kp, c->kz, c->red.sc, s);
+      launched("update_p");
+    }
+  }
+  // true residual ||b - H^ x|| / ||b||
+  launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s);
+  launched("apply");
+  launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s);
+  launched("resid_sq");
+  cuda_ok(cudaEventRecord(c->ev1, s), "event");
+  read_scalars(c, s);
+  inf.true_rel_residual = bb > 0 ? std::sqrt(c->host_sc[S_TRUE] / bb) : 0.0;
+  float ms = 0.f;
+  cuda_ok(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event time");
+  inf.solve_ms = ms;
+  if (info) *info = inf;
+  return st;
+}
+
+void check_solve_params(const hmg_solve_params* p) {
+  require(p != nullptr, "params is NULL");
+  require(p->precision == HMG_PRECISION_FP64 || p->precision == HMG_PRECISION_MIXED, "bad precision");
+  require(p->krylov == HMG_KRYLOV_CG || p->krylov == HMG_KRYLOV_FCG, "bad krylov");
+  require(p->rtol > 0.0 && p->rtol < 1.0, "rtol must be in (0, 1)");
+  require(p->max_iter >= 1 && p->max_iter <= 100000, "max_iter must be in [1, 100000]");
+  check_cycle_params(p->nu_pre, p->nu_post, p->n_coarse);
+}
+
+void need_assembled(const hmg_ctx* c) {
+  if (!c->assembled) throw Fail{HMG_ERR_STATE, "operator not assembled (call hmg_assemble_helmholtz)"};
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hmg_status_string(hmg_status s) {
+  switch (s) {
+    case HMG_OK: return "ok";
+    case HMG_ERR_INVALID_ARG: return "invalid argument";
+    case HMG_ERR_CUDA: return "CUDA error";
+    case HMG_ERR_OOM: return "out of memory";
+    case HMG_ERR_NOT_CONVERGED: return "not converged";
+    case HMG_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HMG_ERR_NONFINITE: return "non-finite value";
+    case HMG_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* hmg_last_error(const hmg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_build_error.c_str();
+}
+
+hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
+  if (!out) {
+    g_build_error = "out is NULL";
+    return HMG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  hmg_ctx* c = nullptr;
+  hmg_status st = guarded(nullptr, [&] {
+    require(p != nullptr, "params is NULL");
+    require(p->refinement >= 0 && p->refinement <= 10, "refinement must be in [0, 10]");
+    require(p->nlayers >= 1 && p->nlayers <= 1024, "nlayers must be in [1, 1024]");
+    require(p->nlevels >= 1 && p->nlevels <= p->refinement + 1, "nlevels must be in [1, refinement + 1]");
+    require(p->radius_m > 0 && std::isfinite(p->radius_m), "radius_m must be positive");
+    require(p->thickness_m > 0 && std::isfinite(p->thickness_m), "thickness_m must be positive");
+    std::vector<HostLevel> host = build_mesh_hierarchy(p->refinement, p->nlevels);
+    c = new hmg_ctx();
+    c->mp = *p;
+    c->lv.resize(host.size());
+    for (size_t k = 0; k < host.size(); ++k) {
+      Level& L = c->lv[k];
+      HostLevel& H = host[k];
+      L.refinement = H.refinement;
+      L.nc = H.ncols;
+      L.ncp = (H.ncols + TW - 1) / TW * TW;
+      L.nz = p->nlayers;
+      L.N = (int64_t)L.nc * L.nz;
+      L.Np = (int64_t)L.ncp * L.nz;
+      L.centroid_host = H.centroid;
+      L.nbr_host = H.nbr;
+      std::vector<int4> nb(L.ncp);
+      for (int col = 0; col < L.ncp; ++col) {
+        if (col < L.nc) nb[col] = make_int4(H.nbr[3 * col], H.nbr[3 * col + 1], H.nbr[3 * col + 2], 0);
+        else nb[col] = make_int4(col, col, col, 0);
+      }
+      std::vector<double> verts((size_t)L.ncp * 9, 0.0);
+      std::copy(H.verts.begin(), H.verts.end(), verts.begin());
+      L.nbr = dalloc<int4>(c, L.ncp);
+      L.verts = dalloc<double>(c, (size_t)L.ncp * 9);
+      cuda_ok(cudaMemcpy(L.nbr, nb.data(), nb.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
+      cuda_ok(cudaMemcpy(L.verts, verts.data(), verts.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+      L.A1 = dalloc<double>(c, L.ncp);
+      L.sigma = dalloc<double4_32a>(c, L.ncp);
+      L.gh = dalloc<double4_32a>(c, L.ncp);
+      L.gh32 = dalloc<float4>(c, L.ncp);
+      L.d = dalloc<double>(c, L.Np);
+      L.e = dalloc<double>(c, L.Np);
+      L.lo = dalloc<double>(c, L.Np);
+      L.w = dalloc<double>(c, L.Np);
+      L.d32 = dalloc<float>(c, L.Np);
+      L.e32 = dalloc<float>(c, L.Np);
+      L.lo32 = dalloc<float>(c, L.Np);
+      L.w32 = dalloc<float>(c, L.Np);
+      L.theta = dalloc<double>(c, L.Np);
+      L.b64 = dalloc<double>(c, L.Np);
+      L.ua64 = dalloc<double>(c, L.Np);
+      L.ub64 = dalloc<double>(c, L.Np);
+      L.ux64 = dalloc<double>(c, L.Np);
+      L.b32 = dalloc<float>(c, L.Np);
+      L.ua32 = dalloc<float>(c, L.Np);
+      L.ub32 = dalloc<float>(c, L.Np);
+      L.ux32 = dalloc<float>(c, L.Np);
+      L.y32 = dalloc<float>(c, L.Np);
+    }
+    const int64_t Np0 = c->lv[0].Np;
+    c->kx = dalloc<double>(c, Np0);
+    c->kr = dalloc<double>(c, Np0);
+    c->kz = dalloc<double>(c, Np0);
+    c->kp = dalloc<double>(c, Np0);
+    c->kq = dalloc<double>(c, Np0);
+    c->kb = dalloc<double>(c, Np0);
+    c->kcol = dalloc<double>(c, Np0);
+    c->kcol2 = dalloc<double>(c, Np0);
+    c->red.partials = dalloc<double>(c, 2 * RED_MAX_BLOCKS);
+    c->red.counter = dalloc<unsigned int>(c, 4);
+    c->red.sc = dalloc<double>(c, S_COUNT);
+    cuda_ok(cudaHostAlloc((void**)&c->host_sc, S_COUNT * sizeof(double), cudaHostAllocDefault), "host alloc");
+    cuda_ok(cudaEventCreate(&c->ev0), "event");
+    cuda_ok(cudaEventCreate(&c->ev1), "event");
+    cuda_ok(cudaDeviceSynchronize(), "build");
+  });
+  if (st != HMG_OK) {
+    if (c) {
+      g_build_error = g_build_error.empty() ? c->err : g_build_error;
+      release(c);
+      delete c;
+    }
+    return st;
+  }
+  *out = c;
+  return HMG_OK;
+}
+
+hmg_status hmg_destroy(hmg_ctx* ctx) {
+  if (!ctx) return HMG_OK;
+  cudaDeviceSynchronize();
+  release(ctx);
+  delete ctx;
+  return HMG_OK;
+}
+
+hmg_status hmg_get_level_info(const hmg_ctx* ctx, int level, hmg_level_info* out) {
+  if (!ctx || !out || level < 0 || level >= (int)ctx->lv.size()) return HMG_ERR_INVALID_ARG;
+  const Level& L = ctx->lv[level];
+  out->refinement = L.refinement;
+  out->ncols = L.nc;
+  out->ncols_padded = L.ncp;
+  out->nlayers = L.nz;
+  out->ncells = L.N;
+  out->ncells_padded = L.Np;
+  return HMG_OK;
+}
+
+hmg_status hmg_export_mesh(const hmg_ctx* ctx, int level, double* centroids, int32_t* nbr) {
+  if (!ctx || level < 0 || level >= (int)ctx->lv.size()) return HMG_ERR_INVALID_ARG;
+  const Level& L = ctx->lv[level];
+  if (centroids) std::memcpy(centroids, L.centroid_host.data(), L.centroid_host.size() * sizeof(double));
+  if (nbr) std::memcpy(nbr, L.nbr_host.data(), L.nbr_host.size() * sizeof(int32_t));
+  return HMG_OK;
+}
+
+hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const double* theta, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(p != nullptr, "params is NULL");
+    require(p->c > 0 && std::isfinite(p->c), "c must be positive");
+    require(p->N >= 0 && std::isfinite(p->N), "N must be >= 0");
+    require(p->nu_cfl > 0 && std::isfinite(p->nu_cfl), "nu_cfl must be positive");
+    require(p->omega > 0 && p->omega < 2, "omega must be in (0, 2)");
+    cudaStream_t s = as_stream(stream);
+    ctx->assembled = false;
+    ctx->op = *p;
+    double dx = p->dx_m > 0 ? p->dx_m : 90.0e3 * std::ldexp(1.0, 6 - ctx->mp.refinement);
+    double dt = p->nu_cfl * dx / p->c;
+    double wc = 0.5 * p->c * dt, wn = 0.5 * p->N * dt;
+    Phys& ph = ctx->ph;
+    ph.R = ctx->mp.radius_m;
+    ph.dz = ctx->mp.thickness_m / ctx->mp.nlayers;
+    ph.wc2 = wc * wc;
+    ph.vfac = wc * wc / (1.0 + wn * wn);
+    ph.omega = p->omega;
+    ctx->has_theta = theta != nullptr;
+    if (theta) {
+      launch_to_tiled(ctx->lv[0], HMG_FP64, theta, ctx->lv[0].theta, s);
+      launched("theta");
+      for (size_t k = 1; k < ctx->lv.size(); ++k) {
+        launch_theta_restrict(ctx->lv[k - 1], ctx->lv[k], s);
+        launched("theta_restrict");
+      }
+    }
+    for (Level& L : ctx->lv) {
+      double* th = L.theta;
+      if (!theta) L.theta = nullptr;  // bands use theta = 1
+      launch_geometry(L, s);
+      launched("geometry");
+      launch_couplings(L, ph.wc2 * ph.dz, s);
+      launched("couplings");
+      launch_bands(L, ph, s);
+      launched("bands");
+      L.theta = th;
+      launch_ldl(L, ph.omega, s);
+      launched("ldl");
+      launch_to_fp32(L, s);
+      launched("to_fp32");
+    }
+    cuda_ok(cudaStreamSynchronize(s), "assemble");
+    ctx->assembled = true;
+  });
+}
+
+hmg_status hmg_apply(hmg_ctx* ctx, int level, int dtype, int layout, const void* x, void* y, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(level >= 0 && level < (int)ctx->lv.size(), "bad level");
+    require(dtype == HMG_FP64 || dtype == HMG_FP32, "bad dtype");
+    require(layout == HMG_LAYOUT_COLUMN || layout == HMG_LAYOUT_TILED, "bad layout");
+    require(x && y && x != y, "x and y must be distinct non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    Level& L = ctx->lv[level];
+    if (layout == HMG_LAYOUT_TILED) {
+      launch_apply(L, dtype, x, y, nullptr, s);
+      launched("apply");
+      return;
+    }
+    launch_to_tiled(L, dtype, x, ctx->kcol, s);
+    launched("to_tiled");
+    launch_apply(L, dtype, ctx->kcol, ctx->kcol2, nullptr, s);
+    launched("apply");
+    launch_to_column(L, dtype, ctx->kcol2, y, s);
+    launched("to_column");
+  });
+}
+
+hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r, void* z, int nu_pre, int nu_post,
+                      int n_coarse, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(precision == HMG_PRECISION_FP64 || precision == HMG_PRECISION_MIXED, "bad precision");
+    require(layout == HMG_LAYOUT_COLUMN || layout == HMG_LAYOUT_TILED, "bad layout");
+    require(r && z && r != z, "r and z must be distinct non-NULL device pointers");
+    check_cycle_params(nu_pre, nu_post, n_coarse);
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    CycleCfg cfg;
+    cfg.nu_pre = nu_pre;
+    cfg.nu_post = nu_post;
+    cfg.n_coarse = n_coarse;
+    cfg.mixed = precision == HMG_PRECISION_MIXED;
+    cfg.omega = ctx->ph.omega;
+    Level& L = ctx->lv[0];
+    if (layout == HMG_LAYOUT_TILED) {
+      cycle(ctx, cfg, 0, r, HMG_FP64, z, HMG_FP64, s);
+      return;
+    }
+    launch_to_tiled(L, HMG_FP64, r, ctx->kcol, s);
+    launched("to_tiled");
+    cycle(ctx, cfg, 0, ctx->kcol, HMG_FP64, ctx->kcol2, HMG_FP64, s);
+    launch_to_column(L, HMG_FP64, ctx->kcol2, z, s);
+    launched("to_column");
+  });
+}
+
+hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_params* params,
+                     hmg_solve_info* info, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  hmg_status result = HMG_OK;
+  hmg_status st = guarded(ctx, [&] {
+    check_solve_params(params);
+    require(b && x, "b and x must be non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    Level& L = ctx->lv[0];
+    launch_to_tiled(L, HMG_FP64, b, ctx->kb, s);
+    launched("to_tiled");
+    result = solve_tiled(ctx, *params, info, s);
+    launch_to_column(L, HMG_FP64, ctx->kx, x, s);
+    launched("to_column");
+    cuda_ok(cudaStreamSynchronize(s), "solve");
+  });
+  if (st != HMG_OK) return st;
+  if (result == HMG_ERR_NOT_CONVERGED) ctx->err = "maximum number of iterations reached";
+  if (result == HMG_ERR_BREAKDOWN) ctx->err = "CG breakdown: p.q <= 0 or r.z <= 0";
+  if (result == HMG_ERR_NONFINITE) ctx->err = "non-finite residual";
+  return result;
+}
+
+hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host, const hmg_solve_params* params,
+                          hmg_solve_info* info, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  hmg_status result = HMG_OK;
+  hmg_status st = guarded(ctx, [&] {
+    check_solve_params(params);
+    require(b_host && x_host, "b_host and x_host must be non-NULL");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    Level& L = ctx->lv[0];
+    cuda_ok(cudaMemcpyAsync(ctx->kcol, b_host, (size_t)L.N * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
+    launch_to_tiled(L, HMG_FP64, ctx->kcol, ctx->kb, s);
+    launched("to_tiled");
+    result = solve_tiled(ctx, *params, info, s);
+    launch_to_column(L, HMG_FP64, ctx->kx, ctx->kcol, s);
+    launched("to_column");
+    cuda_ok(cudaMemcpyAsync(x_host, ctx->kcol, (size_t)L.N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    cuda_ok(cudaStreamSynchronize(s), "solve");
+  });
+  if (st != HMG_OK) return st;
+  return result;
+}
+
+hmg_status hmg_theta_grad(hmg_ctx* ctx, const double* p, const double* lambda, double* grad, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(p && lambda && grad, "p, lambda and grad must be non-NULL device pointers");
+    need_assembled(ctx);
+    Level& L = ctx->lv[0];
+    double* th = L.theta;
+    if (!ctx->has_theta) L.theta = nullptr;
+    launch_theta_grad(L, ctx->ph, p, lambda, grad, as_stream(stream));
+    L.theta = th;
+    launched("theta_grad");
+  });
+}
+
+hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* src, int dst_layout, double* dst,
+                         void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(level >= 0 && level < (int)ctx->lv.size(), "bad level");
+    require(src && dst && src != dst, "src and dst must be distinct non-NULL device pointers");
+    require((src_layout == HMG_LAYOUT_COLUMN && dst_layout == HMG_LAYOUT_TILED) ||
+                (src_layout == HMG_LAYOUT_TILED && dst_layout == HMG_LAYOUT_COLUMN),
+            "layouts must differ");
+    Level& L = ctx->lv[level];
+    if (src_layout == HMG_LAYOUT_COLUMN) launch_to_tiled(L, HMG_FP64, src, dst, as_stream(stream));
+    else launch_to_column(L, HMG_FP64, src, dst, as_stream(stream));
+    launched("layout");
+  });
+}
+
+hmg_status hmg_sync(hmg_ctx* ctx, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] { cuda_ok(cudaStreamSynchronize(as_stream(stream)), "sync"); });
+}
+
+}  // extern "C"

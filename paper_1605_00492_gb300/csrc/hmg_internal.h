@@ -1,0 +1,142 @@
+// Internal declarations of the GB300 Helmholtz multigrid library.
+//
+// Device storage per level (all vectors in the TILED layout of hmg.h:
+// tiles of 32 columns, layer-major inside a tile, so that one warp holding
+// 32 columns reads one layer of all of them with a single coalesced access):
+//   nbr   int4[ncp]      three neighbour columns (w unused)
+//   gh    double4_32a[ncp]   horizontal couplings g_k = w_c^2 / Mh_ff of the three
+//                        lateral faces and their sum G (layer independent)
+//   d, e  double[Np]     diagonal of H^ and the vertical off-diagonal
+//                        H^[(c,l),(c,l-1)] (e = 0 at l = 0)
+//   lo, w double[Np]     L D L^T factors of H^_z: multipliers l_l (0 at l = 0)
+//                        and omega / D_l
+//   *32                  FP32 copies for the mixed-precision cycle
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hmg.h"
+
+namespace hmg {
+
+constexpr int TW = 32;                 // columns per tile
+constexpr int RED_MAX_BLOCKS = 2048;   // partial sums of one reduction
+
+struct HostLevel {
+  int refinement = 0;
+  int ncols = 0;
+  std::vector<double> verts;      // ncols * 9: three unit-sphere vertices per column
+  std::vector<double> centroid;   // ncols * 3
+  std::vector<int32_t> nbr;       // ncols * 3
+};
+
+std::vector<HostLevel> build_mesh_hierarchy(int refinement, int nlevels);
+
+struct Level {
+  int refinement = 0, nc = 0, ncp = 0, nz = 0;
+  int64_t N = 0, Np = 0;
+  std::vector<double> centroid_host;
+  std::vector<int32_t> nbr_host;
+  // geometry
+  int4* nbr = nullptr;
+  double* verts = nullptr;    // ncp * 9
+  double* A1 = nullptr;       // ncp, unit-sphere flat-triangle area
+  double4_32a* sigma = nullptr;   // ncp, RT0 shape factors of the three edges
+  // coefficients
+  double4_32a* gh = nullptr;
+  float4* gh32 = nullptr;
+  double *d = nullptr, *e = nullptr, *lo = nullptr, *w = nullptr;
+  float *d32 = nullptr, *e32 = nullptr, *lo32 = nullptr, *w32 = nullptr;
+  double* theta = nullptr;    // Np
+  // cycle work vectors
+  // b: right-hand side of this level (restricted residual); ua, ub: smoother
+  // ping-pong; ux: result of this level's cycle (the coarse correction)
+  double *b64 = nullptr, *ua64 = nullptr, *ub64 = nullptr, *ux64 = nullptr;
+  float *b32 = nullptr, *ua32 = nullptr, *ub32 = nullptr, *ux32 = nullptr, *y32 = nullptr;
+};
+
+// Slots of the Krylov scalars kept on the device.
+enum Scalar {
+  S_BB = 0, S_RZ, S_PQ, S_RR, S_ALPHA, S_BETA, S_ZQ, S_RZNEW, S_TRUE, S_FLAG, S_COUNT = 16
+};
+// Flag bits raised by reduction epilogues.
+enum { F_NONFINITE = 1, F_BREAKDOWN = 2 };
+// What the last block of a reduction does with the sums.
+enum Epilogue {
+  EPI_STORE0 = 0,   // sc[slot] = s0
+  EPI_ALPHA,        // sc[PQ] = s0; sc[ALPHA] = sc[RZ] / s0
+  EPI_RR,           // sc[RR] = s0 (flag non-finite)
+  EPI_BETA_CG,      // sc[BETA] = s0 / sc[RZ]; sc[RZ] = s0
+  EPI_BETA_FCG,     // sc[BETA] = -sc[ALPHA] * s1 / sc[RZ]; sc[RZ] = s0
+  EPI_INIT_RZ       // sc[RZ] = s0 (flag non-positive)
+};
+
+struct Reduce {
+  double* partials = nullptr;   // RED_MAX_BLOCKS * 2
+  unsigned int* counter = nullptr;
+  double* sc = nullptr;         // S_COUNT scalars
+  int epilogue = EPI_STORE0;
+  int slot = 0;
+};
+
+struct Phys {
+  double R = 0, dz = 0, wc2 = 0, vfac = 0, omega = 0.8;
+};
+
+// ---- assembly (assemble.cu)
+void launch_geometry(const Level& L, cudaStream_t s);
+void launch_couplings(const Level& L, double wc2_dz, cudaStream_t s);
+void launch_bands(const Level& L, const Phys& ph, cudaStream_t s);
+void launch_ldl(const Level& L, double omega, cudaStream_t s);
+void launch_to_fp32(const Level& L, cudaStream_t s);
+void launch_theta_restrict(const Level& fine, const Level& coarse, cudaStream_t s);
+void launch_theta_grad(const Level& L, const Phys& ph, const double* p_col, const double* lam_col,
+                       double* grad_col, cudaStream_t s);
+
+// ---- cycle kernels (cycle.cu); dt = HMG_FP64 or HMG_FP32 names the type of
+// each void* buffer.
+void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, float* bcopy,
+                   double omega, cudaStream_t s);
+void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo, int uo_dt,
+                  void* ytmp, const void* ec, int ec_dt, double omega, cudaStream_t s);
+void launch_prolong(const Level& L, int dt, void* u, const void* ec, int ec_dt, cudaStream_t s);
+void launch_resid_restrict(const Level& L, int dt, const void* b, const void* u, void* bc, int bc_dt,
+                           cudaStream_t s);
+void launch_apply(const Level& L, int dt, const void* x, void* y, const Reduce* red, cudaStream_t s);
+
+// ---- Krylov vector kernels (krylov.cu), FP64, tiled layout of level L
+void launch_to_tiled(const Level& L, int dt, const void* col, void* tiled, cudaStream_t s);
+void launch_to_column(const Level& L, int dt, const void* tiled, void* col, cudaStream_t s);
+void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,
+                const Reduce& red, cudaStream_t s);  // s0 = a.b, s1 = c.d (c may be null)
+void launch_update_xr(const Level& L, double* x, double* r, const double* p, const double* q,
+                      const Reduce& red, cudaStream_t s);
+void launch_update_p(const Level& L, double* p, const double* z, const double* sc, cudaStream_t s);
+void launch_resid_sq(const Level& L, const double* b, const double* q, const Reduce& red,
+                     cudaStream_t s);  // s0 = |b - q|^2
+void launch_check_finite(const Level& L, const double* v, const Reduce& red, cudaStream_t s);
+
+int reduce_grid(int64_t n);
+
+}  // namespace hmg
+
+struct hmg_ctx {
+  hmg_mesh_params mp{};
+  hmg_op_params op{};
+  hmg::Phys ph{};
+  bool assembled = false;
+  bool has_theta = false;
+  std::vector<hmg::Level> lv;
+  // Krylov vectors on the finest level (tiled) and a column-layout staging buffer
+  double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr, *kb = nullptr;
+  double *kcol = nullptr, *kcol2 = nullptr;
+  hmg::Reduce red{};
+  double* host_sc = nullptr;      // page-locked copy of the scalars
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<void*> allocations;
+  std::string err;
+};

@@ -1,0 +1,128 @@
+// FP64 vector kernels of the outer Krylov solve (Sec. 5) on the finest level,
+// tiled layout, and the COLUMN <-> TILED layout conversions.  Every kernel
+// that needs a global dot product folds it into the same pass (deterministic
+// grid reduction, reduce.cuh) and forms the Krylov scalar on the device.
+#include "hmg_internal.h"
+#include "reduce.cuh"
+
+namespace hmg {
+
+namespace {
+
+__device__ __forceinline__ bool decode(int64_t t, int nz, int nc, int& c, int& l) {
+  int lane = (int)(t & 31);
+  int64_t tile = t / (TW * nz);
+  l = (int)((t >> 5) % nz);
+  c = (int)(tile * TW + lane);
+  return c < nc;
+}
+
+template <typename T>
+__global__ void k_to_tiled(int nc, int nz, int64_t Np, const T* __restrict__ col, T* __restrict__ tiled) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Np) return;
+  int c, l;
+  tiled[t] = decode(t, nz, nc, c, l) ? col[(int64_t)c * nz + l] : (T)0;
+}
+
+template <typename T>
+__global__ void k_to_column(int nc, int nz, int64_t Np, const T* __restrict__ tiled, T* __restrict__ col) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Np) return;
+  int c, l;
+  if (decode(t, nz, nc, c, l)) col[(int64_t)c * nz + l] = tiled[t];
+}
+
+// s0 = a.b, s1 = c.d (c == nullptr: s1 = 0)
+__global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                      const double* __restrict__ c, const double* __restrict__ d, Reduce red) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s0 += a[i] * b[i];
+    if (c) s1 += c[i] * d[i];
+  }
+  grid_reduce2(s0, s1, red);
+}
+
+// x += alpha p; r -= alpha q; s0 = r.r
+__global__ void k_update_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q, Reduce red) {
+  const double alpha = red.sc[S_ALPHA];
+  double s0 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s0 += ri * ri;
+  }
+  grid_reduce2(s0, 0.0, red);
+}
+
+// p = z + beta p
+__global__ void k_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                           const double* __restrict__ sc) {
+  const double beta = sc[S_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// s0 = |b - q|^2
+__global__ void k_resid_sq(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
+                           Reduce red) {
+  double s0 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = b[i] - q[i];
+    s0 += v * v;
+  }
+  grid_reduce2(s0, 0.0, red);
+}
+
+inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+int reduce_grid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  int cap = 152 * 8;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void launch_to_tiled(const Level& L, int dt, const void* col, void* tiled, cudaStream_t s) {
+  if (dt == HMG_FP64)
+    k_to_tiled<double><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const double*)col, (double*)tiled);
+  else
+    k_to_tiled<float><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const float*)col, (float*)tiled);
+}
+
+void launch_to_column(const Level& L, int dt, const void* tiled, void* col, cudaStream_t s) {
+  if (dt == HMG_FP64)
+    k_to_column<double><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const double*)tiled, (double*)col);
+  else
+    k_to_column<float><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const float*)tiled, (float*)col);
+}
+
+void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,
+                const Reduce& red, cudaStream_t s) {
+  k_dot<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, a, b, c, d, red);
+}
+
+void launch_update_xr(const Level& L, double* x, double* r, const double* p, const double* q,
+                      const Reduce& red, cudaStream_t s) {
+  k_update_xr<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, x, r, p, q, red);
+}
+
+void launch_update_p(const Level& L, double* p, const double* z, const double* sc, cudaStream_t s) {
+  k_update_p<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, p, z, sc);
+}
+
+void launch_resid_sq(const Level& L, const double* b, const double* q, const Reduce& red, cudaStream_t s) {
+  k_resid_sq<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, b, q, red);
+}
+
+void launch_check_finite(const Level& L, const double* v, const Reduce& red, cudaStream_t s) {
+  k_dot<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, v, v, nullptr, nullptr, red);
+}
+
+}  // namespace hmg
