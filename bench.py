@@ -1,0 +1,586 @@
+#!/usr/bin/env python
+"""Benchmark of the lumped pressure-Helmholtz multigrid solve on GB300.
+
+One step = one complete solve H^ x = b (PCG preconditioned by one V-cycle per
+iteration, x0 = 0, stopped at ||r||/||b|| < 1e-8) on the paper-scale shell:
+icosahedral refinement 6 (81,920 columns) x 64 layers, 5 levels, FP64
+(Table "Grid setup", LO).  The right-hand side is seeded N(0,1) per cell, on
+the device before the timed region.  Alongside the FP64 solves/s the line
+reports the mixed form (FP32 V-cycle, FP64 Krylov and coarsest level), the
+V-cycle bandwidth of both forms against the measured HBM peak, the roofline
+of the dominant kernel (timed live with CUDA events inside the timed region),
+an end-to-end number through host buffers, the clocks seen and the CPU oracle
+timed on a bounded sample.
+
+--impl reference times the CPU oracle itself on the same workload (one PCG
+iteration per step, scaled to solves/s by the iteration count of the full
+solve).  Under torchrun every rank solves its own copy of the problem
+(replicas: the solve is not sharded across GPUs), rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "V-cycle HBM GB/s (% of peak); solves/s at 81920x64, FP64 vs mixed @1e-8"
+UNIT = "solves/s"
+WORKLOAD = "r6x64"
+
+
+def workload_desc(name):
+    import hmg_inputs as gi
+    w = gi.WORKLOADS[name]
+    return (f"icosahedral refinement {w['refinement']} ({gi.ncolumns(w['refinement'])} columns) x "
+            f"{w['nlayers']} layers, R = 6371 km, H = 10 km, {w['nlevels']} levels, nu_CFL = 8, omega = 0.8, "
+            "2 pre / 2 post sweeps, 2 coarsest sweeps, PCG to 1e-8")
+# PCG iterations of the full FP64 solve of this workload (oracle and GPU agree;
+# asserted by tests/test_gpu_fullsize.py).  Used to scale the oracle sample.
+ORACLE_ITERATIONS = 11
+
+# Derived FP64 peak of GB300: 152 SMs x 4 sub-partitions, each retiring one
+# 32-lane FP64 FMA warp instruction per 64 cycles (measured: issue interval
+# and dependent latency both 64 cycles), 2 flops per FMA, 2070 MHz maximum SM
+# clock: 152 * 4 * 32 / 64 * 2 * 2.07e9 = 1.259 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 4 * 32 / 64 * 2 * 2.07e9 / 1e12
+FALLBACK_HBM_GBS = 6800.0
+REFERENCE_BUDGET_S = 150.0   # wall time of the --impl reference timed + warm-up steps
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- byte / flop models
+# Algorithmic bytes per fine cell of each kernel (stored coefficients and
+# vectors once per kernel; neighbour re-reads of u are not counted), s = bytes
+# per scalar of the level's type, nz = layers; per-column data (3 neighbour
+# indices + pad = 16 B, 3 couplings + sum = 4 s) is spread over nz cells.
+
+def kernel_bytes_per_cell(kernel, s, nz, s_b=None, s_out=None, s_c=None, fused_prolong=False):
+    s_b = s_b or s
+    s_out = s_out or s
+    s_c = s_c or s
+    col = (16 + 4 * s) / nz
+    if kernel == "sweep0":
+        extra = 4 if (s == 4 and s_b == 8) else 0          # FP32 copy of an FP64 b
+        return s_b + 2 * s + s_out + extra
+    if kernel == "sweep":
+        return 4 * s + s_out + col + (s_c / 4 if fused_prolong else 0)
+    if kernel == "resid_restrict":
+        return 4 * s + s_c / 4 + col
+    if kernel == "prolong":
+        return 2 * s + s_c / 4
+    if kernel == "apply":
+        return 4 * s + col
+    raise ValueError(kernel)
+
+
+# FP64 operations per cell (FMA counted as 2 flops, MUL/ADD as 1)
+KERNEL_FLOPS = {"sweep0": 5, "sweep": 13, "resid_restrict": 12.5, "prolong": 1, "apply": 11}
+
+
+def vcycle_bytes(levels_ncells, nz, mixed, nu_pre=2, nu_post=2, n_coarse=2):
+    """Model bytes of one V-cycle (sum of its kernels)."""
+    total = 0.0
+    L = len(levels_ncells)
+    for lev, n in enumerate(levels_ncells):
+        fp32 = mixed and lev < L - 1
+        s = 4 if fp32 else 8
+        s_c = (4 if (mixed and lev + 1 < L - 1) else 8) if lev < L - 1 else s
+        s_b = 8 if lev == 0 else s
+        out0 = 8 if lev == 0 else s
+        if lev == L - 1:
+            total += n * kernel_bytes_per_cell("sweep0", s, nz, s_b=s_b)
+            total += (n_coarse - 1) * n * kernel_bytes_per_cell("sweep", s, nz)
+            continue
+        sb_after = s  # later kernels read the level's own copy of b
+        total += n * kernel_bytes_per_cell("sweep0", s, nz, s_b=s_b)
+        total += (nu_pre - 1) * n * kernel_bytes_per_cell("sweep", sb_after, nz)
+        total += n * kernel_bytes_per_cell("resid_restrict", s, nz, s_c=s_c)
+        if not fp32:
+            total += n * kernel_bytes_per_cell("prolong", s, nz, s_c=s_c)
+        for i in range(nu_post):
+            last = i == nu_post - 1
+            total += n * kernel_bytes_per_cell("sweep", s, nz, s_out=out0 if last else s, s_c=s_c,
+                                               fused_prolong=(fp32 and i == 0))
+    return total
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def mark(self, start):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def summary(self):
+        import datetime
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def stamp(x):
+            try:
+                return datetime.datetime.strptime(x, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                return None
+
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
+        inside = [r for r in rows if t0 and t1 and stamp(r[0]) is not None and t0 - 0.05 <= stamp(r[0]) <= t1 + 0.05]
+        window = "timed region" if inside else "whole run (no sample inside the timed region)"
+        rows = inside or rows
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "window": window,
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device):
+    """Max of a float over all ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(workload, pcg_iterations, threads_note=True):
+    """Time the oracle's first `pcg_iterations` PCG iterations (setup excluded)."""
+    import numpy as np  # noqa: F401
+    import hmg_inputs as gi
+    from oracle import helmholtz, krylov, mesh, multigrid
+    w = gi.WORKLOADS[workload]
+    t0 = time.perf_counter()
+    ms = mesh.hierarchy(w["refinement"], w["nlevels"])
+    prm = helmholtz.Params(refinement=w["refinement"], nlayers=w["nlayers"])
+    ops = helmholtz.assemble_hierarchy(ms, prm)
+    setup_s = time.perf_counter() - t0
+    b = gi.rhs(ops[0].ncells)
+    t0 = time.perf_counter()
+    krylov.pcg(ops[0].H.dot, lambda v: multigrid.vcycle(ops, v), b, rtol=1e-8, max_iter=pcg_iterations)
+    return time.perf_counter() - t0, setup_s
+
+
+def cpu_baseline_subprocess(workload, iterations):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, "--oracle-iterations",
+           str(iterations)]
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": res.stderr[-400:]}
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    # pcg(max_iter=k) runs k + 1 V-cycles and k operator applications; the
+    # full solve runs ORACLE_ITERATIONS + 1 V-cycles.
+    solve_s = d["seconds"] * (ORACLE_ITERATIONS + 1) / (iterations + 1)
+    return {"value": 1.0 / solve_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"first {iterations} of {ORACLE_ITERATIONS} PCG iterations of the {workload} FP64 solve "
+                       f"({d['seconds']:.1f} s; setup {d['setup_s']:.1f} s excluded), scaled by "
+                       f"{ORACLE_ITERATIONS + 1}/{iterations + 1} V-cycles to one solve; NumPy/SciPy, one thread"),
+            "seconds_per_solve": solve_s}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import hmg_inputs as gi
+    import paper_1605_00492_gb300 as hmg
+    w = gi.WORKLOADS[args.workload]
+    r, nz, L = w["refinement"], w["nlayers"], w["nlevels"]
+    h = hmg.Hierarchy(r, nz, L)
+    h.assemble()
+    n = h.ncells
+    stream = torch.cuda.current_stream()
+    b = torch.tensor(gi.rhs(n), dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    kw64 = dict(precision="fp64", krylov="cg", rtol=1e-8, max_iter=200)
+    kwmx = dict(precision="mixed", krylov="fcg", rtol=1e-8, max_iter=200)
+
+    # warm-up; one traced solve per form gives the per-kernel, per-level breakdown
+    for _ in range(args.warmup):
+        h.solve(b, out=x, **kw64)
+    h.profile_start()
+    _, info64 = h.solve(b, out=x, **kw64)
+    br64 = h.profile_stop()
+    for _ in range(args.warmup):
+        h.solve(b, out=x, **kwmx)
+    h.profile_start()
+    _, infomx = h.solve(b, out=x, **kwmx)
+    brmx = h.profile_stop()
+    (dom_k, dom_l), _ = max(br64.items(), key=lambda kv: kv[1][1])
+
+    # ---- timed region: K FP64 solves, dominant kernel traced live
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = h.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        h.profile_start(kernels=[dom_k], levels=[dom_l])
+        clk.mark(True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, info = h.solve(b, out=x, **kw64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk.mark(False)
+        dom_stats = h.profile_stop()
+    barrier(world)
+    launches = h.launch_count() - launches0
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    clocks = clk.summary()
+    ms64 = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms / 1e3)
+
+    # ---- mixed form, same protocol (no tracing)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, infomx = h.solve(b, out=x, **kwmx)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    msmx = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+
+    # ---- V-cycle alone (tiled layout, no conversions), both forms
+    hbm, hbm_src = measured_peaks()
+    ncells_levels = [lv["ncells"] for lv in h.levels]
+    rt = h.to_layout(b, "column", "tiled")
+    zt = torch.empty_like(rt)
+    vc = {}
+    for form in ("fp64", "mixed"):
+        for _ in range(3):
+            h.vcycle(rt, precision=form, layout="tiled", out=zt)
+        reps = max(10, args.steps)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            h.vcycle(rt, precision=form, layout="tiled", out=zt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        byts = vcycle_bytes(ncells_levels, nz, form == "mixed")
+        gbs = byts / (ms * 1e-3) / 1e9
+        vc[form] = {"ms": round(ms, 4), "model_bytes": int(byts), "GB_s": round(gbs, 1),
+                    "frac_of_hbm_peak": round(gbs / hbm, 4)}
+
+    # ---- end to end: host buffers through the C ABI (H2D + solve + D2H)
+    e2e = None
+    if not args.no_e2e:
+        bh = b.cpu().pin_memory()
+        xh = torch.empty_like(bh).pin_memory()
+        for _ in range(2):
+            h.solve_host(bh, xh, **kw64)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            h.solve_host(bh, xh, **kw64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+        e2e = {"value": round(world / (ms_e2e / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": int(n * 8),
+               "d2h_bytes_per_step": int(n * 8), "ms_per_step": round(ms_e2e, 4)}
+
+    # ---- roofline of the dominant kernel
+    cnt, tot = dom_stats.get((dom_k, dom_l), (0, 0.0))
+    n_l = ncells_levels[dom_l]
+    per_cell_b = kernel_bytes_per_cell(dom_k, 8, nz)
+    avg_ms = tot / max(cnt, 1)
+    gbs = per_cell_b * n_l / (avg_ms * 1e-3) / 1e9
+    tflops = KERNEL_FLOPS[dom_k] * n_l / (avg_ms * 1e-3) / 1e12
+    t_hbm = per_cell_b * n_l / (hbm * 1e9)
+    t_alu = KERNEL_FLOPS[dom_k] * n_l / (FP64_PEAK_TFLOPS * 1e12)
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "derived FP64 FMA rate (152 SM x 4 x 32 lanes / 64 cycles x 2 x 2.07 GHz)",
+                "hbm_achieved_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs / hbm, 4), "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof.update({"kernel": f"{dom_k}@level{dom_l}", "launches": cnt, "avg_us": round(avg_ms * 1e3, 2),
+                 "bytes_per_launch": int(per_cell_b * n_l), "flops_per_launch": int(KERNEL_FLOPS[dom_k] * n_l),
+                 "traffic": args.traffic})
+
+    def breakdown(br):
+        return {f"{k}@{lvl}": {"launches": c, "ms": round(t, 3)} for (k, lvl), (c, t) in sorted(br.items())}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms64, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {workload_desc(args.workload)}", "ncols": h.levels[0]["ncols"], "nlayers": nz,
+                   "ncells": n, "nlevels": L, "rhs": "N(0,1) per cell, seed 0", "krylov": "CG",
+                   "l2": "working set > 1 GB, larger than the 126 MB L2: no flush"},
+        "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+        "mixed": {"solves_per_s": round(world / (msmx / 1e3), 3), "ms_per_solve": round(msmx, 4),
+                  "iterations": infomx["iterations"], "true_rel_residual": infomx["true_rel_residual"],
+                  "krylov": "flexible CG", "dtype": "f32 cycle / f64 Krylov + coarsest"},
+        "vcycle": vc,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "breakdown_fp64_one_solve": breakdown(br64),
+        "breakdown_mixed_one_solve": breakdown(brmx),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_subprocess(args.workload, args.oracle_iterations)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+def oracle_vcycle_primitives(ops, get_rhs, omega=0.8, nu_pre=2, nu_post=2, n_coarse=2):
+    """One oracle V-cycle as a list of its primitive calls.
+
+    Calling the returned callables in order performs, with the oracle's own
+    routines (multigrid.smooth / restrict / prolong, the sparse H^ product),
+    exactly what multigrid.vcycle(ops, get_rhs()) does, in the same order;
+    the result is then in u[0].  Returns (calls, u).
+    """
+    import numpy as np
+    from oracle import multigrid
+    L = len(ops)
+    u = [None] * L
+    rhs = [None] * L
+
+    def zero(l):
+        return lambda: u.__setitem__(l, np.zeros_like(rhs[l]))
+
+    def smooth(l):
+        return lambda: u.__setitem__(l, multigrid.smooth(ops[l], u[l], rhs[l], omega))
+
+    def restrict(l):
+        return lambda: rhs.__setitem__(l + 1, multigrid.restrict(rhs[l] - ops[l].H @ u[l], ops[l + 1].ncols,
+                                                                 ops[l].nlayers))
+
+    def prolong(l):
+        return lambda: u.__setitem__(l, u[l] + multigrid.prolong(u[l + 1], ops[l + 1].ncols, ops[l].nlayers))
+
+    calls = [lambda: rhs.__setitem__(0, get_rhs())]
+    for l in range(L - 1):
+        calls.append(zero(l))
+        calls += [smooth(l)] * nu_pre
+        calls.append(restrict(l))
+    calls.append(zero(L - 1))
+    calls += [smooth(L - 1)] * n_coarse
+    for l in range(L - 2, -1, -1):
+        calls.append(prolong(l))
+        calls += [smooth(l)] * nu_post
+    return calls, u
+
+
+def oracle_pcg_primitives(ops, b, state=None):
+    """The oracle's PCG iterations as an endless stream of primitive calls:
+    yields (index within the iteration, calls per iteration, callable).
+    `state` (optional dict) receives the iterates x, r, p."""
+    import numpy as np
+    st = state if state is not None else {}
+    st.update({"r": b.copy(), "x": np.zeros_like(b), "p": None, "rz": None})
+
+    def krylov_update(u):
+        def f():
+            z = u[0]
+            rz = float(np.dot(st["r"], z))
+            st["p"] = z.copy() if st["p"] is None else z + (rz / st["rz"]) * st["p"]
+            st["rz"] = rz
+            q = ops[0].H @ st["p"]
+            alpha = rz / float(np.dot(st["p"], q))
+            st["x"] = st["x"] + alpha * st["p"]
+            st["r"] = st["r"] - alpha * q
+        return f
+
+    while True:
+        calls, u = oracle_vcycle_primitives(ops, lambda: st["r"])
+        calls.append(krylov_update(u))
+        for i, fn in enumerate(calls):
+            yield i, len(calls), fn
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import hmg_inputs as gi
+    from oracle import helmholtz, mesh
+    w = gi.WORKLOADS[args.workload]
+    ms = mesh.hierarchy(w["refinement"], w["nlevels"])
+    prm = helmholtz.Params(refinement=w["refinement"], nlayers=w["nlayers"])
+    ops = helmholtz.assemble_hierarchy(ms, prm)
+    b = gi.rhs(ops[0].ncells)
+    stream = oracle_pcg_primitives(ops, b)
+    durations = {}
+
+    def run(count):
+        for _ in range(count):
+            i, P, fn = next(stream)
+            t = time.perf_counter()
+            fn()
+            durations.setdefault(i, []).append(time.perf_counter() - t)
+        return P
+
+    # calibrate one iteration, then size each step so that all K + W steps
+    # take about REFERENCE_BUDGET_S, covering every primitive at least once.
+    t0 = time.perf_counter()
+    P = run(1)
+    P = run(P - 1)
+    t_iter = time.perf_counter() - t0
+    per_prim = t_iter / P
+    chunk = int(max(-(-P // args.steps), min(P, REFERENCE_BUDGET_S / ((args.steps + args.warmup) * per_prim))))
+    chunk = max(chunk, 1)
+    for _ in range(args.warmup):
+        run(chunk)
+    durations.clear()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run(chunk)
+    total = time.perf_counter() - t0
+    iter_s = sum(statistics.mean(durations[i]) for i in range(P) if i in durations)
+    covered = sum(1 for i in range(P) if i in durations)
+    value = 1.0 / (iter_s * (ORACLE_ITERATIONS + 1))
+    sample = (f"each step: {chunk} of the {P} primitive calls (line relaxation, residual+restriction, "
+              f"prolongation, CG update) of one oracle PCG iteration of the {args.workload} FP64 solve; "
+              f"iteration time = sum of the mean time of each primitive ({covered}/{P} observed); "
+              f"solves/s = 1 / ({ORACLE_ITERATIONS + 1} x iteration time: {ORACLE_ITERATIONS} iterations + the "
+              "initial V-cycle); NumPy/SciPy, one thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {workload_desc(args.workload)}"},
+           "seconds_per_pcg_iteration": round(iter_s, 4),
+           "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-iterations", type=int, default=2)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.oracle_sample is None:
+        ap.error("--warmup must be >= 3")
+    if args.oracle_sample:
+        sec, setup = oracle_sample(args.oracle_sample, args.oracle_iterations)
+        print(json.dumps({"seconds": sec, "setup_s": setup}))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -60,7 +60,7 @@ typedef enum { HMG_KRYLOV_CG = 0, HMG_KRYLOV_FCG = 1 } hmg_krylov;
 /* Shell and hierarchy (Sec. 3.1, Sec. 4.1, Table "Grid setup"). */
 typedef struct {
   int refinement;       /* finest icosahedral refinement r >= 0 (20 * 4^r columns) */
-  int nlayers;          /* vertical layers, 1 <= nlayers <= 1024 */
+  int nlayers;          /* vertical layers, 1 <= nlayers <= 256 */
   int nlevels;          /* multigrid levels, 1 <= nlevels <= refinement + 1 */
   double radius_m;      /* inner radius R of the shell, > 0 (6.371e6) */
   double thickness_m;   /* shell thickness H, > 0 (1.0e4) */
@@ -180,6 +180,47 @@ hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* 
 
 /* Synchronise `stream` and report any pending device error. */
 hmg_status hmg_sync(hmg_ctx* ctx, void* stream);
+
+/* Kernel classes reported by the tracing calls below. */
+typedef enum {
+  HMG_K_SWEEP0 = 0,          /* first line relaxation from u = 0 */
+  HMG_K_SWEEP = 1,           /* line relaxation (with fused prolongation in FP32) */
+  HMG_K_PROLONG = 2,         /* u += P e_c (FP64 cycle) */
+  HMG_K_RESID_RESTRICT = 3,  /* b_c = P^T (b - H^ u) */
+  HMG_K_APPLY = 4,           /* H^ x (outer operator, optionally with p.q) */
+  HMG_K_DOT = 5,
+  HMG_K_UPDATE_XR = 6,       /* x += alpha p, r -= alpha q, r.r */
+  HMG_K_UPDATE_P = 7,        /* p = z + beta p */
+  HMG_K_LAYOUT = 8,          /* COLUMN <-> TILED */
+  HMG_K_RESID_SQ = 9,        /* |b - H^ x|^2 */
+  HMG_K_ASSEMBLY = 10,
+  HMG_K_THETA_GRAD = 11,
+  HMG_K_COUNT = 12
+} hmg_kernel_id;
+
+typedef struct {
+  int kernel;       /* hmg_kernel_id */
+  int level;        /* multigrid level (0 = finest) */
+  int launches;
+  double total_ms;  /* sum of CUDA-event durations of those launches */
+} hmg_kernel_stat;
+
+/* Tracing (the per-level kernel breakdown of Sec. 5.4): from this call on,
+ * every launch of a kernel class whose bit is set in kernel_mask, on a level
+ * whose bit is set in level_mask, is bracketed by CUDA events on its stream.
+ * Any previous records are discarded.  Errors: INVALID_ARG, CUDA. */
+hmg_status hmg_profile_start(hmg_ctx* ctx, unsigned kernel_mask, unsigned level_mask);
+
+/* Stop tracing, synchronise the recorded events and write up to `capacity`
+ * aggregated (kernel, level) records to `out`; *count receives the number of
+ * records available.  Errors: INVALID_ARG, STATE (not started), CUDA. */
+hmg_status hmg_profile_stop(hmg_ctx* ctx, hmg_kernel_stat* out, int capacity, int* count);
+
+/* Number of kernels this context has launched since it was built. */
+hmg_status hmg_launch_count(const hmg_ctx* ctx, int64_t* count);
+
+/* Name of a kernel class ("?" if out of range). */
+const char* hmg_kernel_name(int kernel);
 
 /* Human-readable description of the last error on this context ("" if none),
  * or of the last build failure when ctx is NULL.  Owned by the library. */

@@ -60,6 +60,15 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("level", ctypes.c_int), ("launches", ctypes.c_int),
+                ("total_ms", ctypes.c_double)]
+
+
+KERNELS = ["sweep0", "sweep", "prolong", "resid_restrict", "apply", "dot", "update_xr", "update_p", "layout",
+           "resid_sq", "assembly", "theta_grad"]
+
+
 class LevelInfo(ctypes.Structure):
     _fields_ = [("refinement", ctypes.c_int), ("ncols", ctypes.c_int), ("ncols_padded", ctypes.c_int),
                 ("nlayers", ctypes.c_int), ("ncells", ctypes.c_int64), ("ncells_padded", ctypes.c_int64)]
@@ -80,6 +89,10 @@ _SIGNATURES = {
     "hmg_theta_grad": [_P, _P, _P, _P, _P],
     "hmg_to_layout": [_P, _I, _I, _P, _I, _P, _P],
     "hmg_sync": [_P, _P],
+    "hmg_profile_start": [_P, ctypes.c_uint, ctypes.c_uint],
+    "hmg_profile_stop": [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)],
+    "hmg_launch_count": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "hmg_kernel_name": [_I],
     "hmg_last_error": [_P],
     "hmg_status_string": [_I],
 }
@@ -99,7 +112,8 @@ def load_library(path=None):
     for name, args in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name in ("hmg_last_error", "hmg_status_string") else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name in ("hmg_last_error", "hmg_status_string", "hmg_kernel_name") \
+            else ctypes.c_int
     if path == LIB_PATH:
         _lib = lib
     return lib
@@ -236,6 +250,27 @@ class Hierarchy:
         self._check(self.lib.hmg_to_layout(self._ctx, level, LAYOUT[src], _ptr(v.contiguous()), LAYOUT[dst],
                                            _ptr(out), _stream(stream)))
         return out
+
+    def profile_start(self, kernels=None, levels=None):
+        """Bracket launches of the named kernel classes on the given levels with
+        CUDA events (all when None)."""
+        kmask = 0xFFFFFFFF if kernels is None else sum(1 << KERNELS.index(k) for k in kernels)
+        lmask = 0xFFFFFFFF if levels is None else sum(1 << int(l) for l in levels)
+        self._check(self.lib.hmg_profile_start(self._ctx, kmask, lmask))
+
+    def profile_stop(self):
+        """Records {(kernel, level): (launches, total_ms)} since profile_start."""
+        cap = 512
+        buf = (KernelStat * cap)()
+        n = _I()
+        self._check(self.lib.hmg_profile_stop(self._ctx, buf, cap, ctypes.byref(n)))
+        return {(KERNELS[buf[i].kernel], buf[i].level): (buf[i].launches, buf[i].total_ms)
+                for i in range(min(n.value, cap))}
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.hmg_launch_count(self._ctx, ctypes.byref(n)))
+        return n.value
 
     def sync(self, stream=None):
         self._check(self.lib.hmg_sync(self._ctx, _stream(stream)))

@@ -52,6 +52,13 @@ void release(hmg_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   c->ev0 = c->ev1 = nullptr;
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  c->capture_stream = nullptr;
 }
 
 template <typename F>
@@ -79,6 +86,46 @@ void require(bool ok, const std::string& msg) {
   if (!ok) throw Fail{HMG_ERR_INVALID_ARG, msg};
 }
 
+// ------------------------------------------------------------ tracing
+
+cudaEvent_t pool_event(hmg_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cuda_ok(cudaEventCreate(&e), "event");
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+int prof_begin(hmg_ctx* c, int kernel, int level, cudaStream_t s) {
+  if (!c->prof_on || !((c->prof_kmask >> kernel) & 1u) || level < 0 || level > 31 ||
+      !((c->prof_lmask >> level) & 1u))
+    return -1;
+  size_t idx = c->ev_used;
+  cudaEvent_t a = pool_event(c);
+  pool_event(c);
+  cuda_ok(cudaEventRecord(a, s), "event");
+  c->prof.push_back(ProfRec{kernel, level, idx});
+  return (int)c->prof.size() - 1;
+}
+
+void prof_end(hmg_ctx* c, int rec, cudaStream_t s) {
+  if (rec < 0) return;
+  cuda_ok(cudaEventRecord(c->ev_pool[c->prof[rec].ev + 1], s), "event");
+}
+
+// Launch `call` (one or more kernels), check the launch, count it and, when
+// tracing selects (kernel, level), bracket it with events.
+#define LAUNCHN(C, K, LEV, S, NK, CALL)              \
+  do {                                               \
+    int rec_ = prof_begin((C), (K), (LEV), (S));     \
+    CALL;                                            \
+    launched(#CALL);                                 \
+    prof_end((C), rec_, (S));                        \
+    (C)->launches += (NK);                           \
+  } while (0)
+#define LAUNCH(C, K, LEV, S, CALL) LAUNCHN(C, K, LEV, S, 1, CALL)
+
 // ------------------------------------------------------------ V-cycle driver
 
 struct CycleCfg {
@@ -97,9 +144,10 @@ void* work(Level& L, int dt, int which) {
 }
 
 // out <- V_lev b (zero initial guess).  b has type b_dt, out has type out_dt;
-// out must not be one of the level's work buffers ua / ub.
+// out must not be one of the level's work buffers ua / ub.  `dot` (optional)
+// is fused into the last sweep of this level.
 void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, void* out, int out_dt,
-           cudaStream_t s) {
+           cudaStream_t s, const SweepDot* dot = nullptr) {
   Level& L = c->lv[lev];
   const int nlev = (int)c->lv.size();
   const int dt = level_dt(c, cfg, lev);
@@ -109,46 +157,43 @@ void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, vo
   void* B = work(L, dt, 1);
   float* bcopy = (dt == HMG_FP32 && b_dt == HMG_FP64) ? L.b32 : nullptr;
 
-  if (coarsest && npre == 1 && out_dt == dt && !bcopy) {
-    launch_sweep0(L, dt, b, b_dt, out, nullptr, cfg.omega, s);
-    launched("sweep0");
+  if (coarsest && npre == 1 && out_dt == dt && !bcopy && !dot) {
+    LAUNCH(c, HMG_K_SWEEP0, lev, s, launch_sweep0(L, dt, b, b_dt, out, nullptr, cfg.omega, s));
     return;
   }
-  launch_sweep0(L, dt, b, b_dt, A, bcopy, cfg.omega, s);
-  launched("sweep0");
+  LAUNCH(c, HMG_K_SWEEP0, lev, s, launch_sweep0(L, dt, b, b_dt, A, bcopy, cfg.omega, s));
   const void* bl = bcopy ? (const void*)bcopy : b;
   void* cur = A;
   void* nxt = B;
   for (int i = 1; i < npre; ++i) {
     bool last = coarsest && i == npre - 1;
-    launch_sweep(L, dt, bl, cur, last ? out : nxt, last ? out_dt : dt, L.y32, nullptr, dt, cfg.omega, s);
-    launched("sweep");
+    LAUNCH(c, HMG_K_SWEEP, lev, s,
+           launch_sweep(L, dt, bl, cur, last ? out : nxt, last ? out_dt : dt, nullptr, dt, cfg.omega,
+                        last ? dot : nullptr, s));
     if (last) return;
     std::swap(cur, nxt);
   }
-  if (coarsest)  // n_coarse == 1 with a result that changes buffer type: not produced by any caller
+  if (coarsest)  // n_coarse == 1 with a dot or a change of type: not produced by any caller
     throw Fail{HMG_ERR_INVALID_ARG, "unsupported coarsest-level configuration"};
   // residual, restricted to the next coarser level
   Level& C = c->lv[lev + 1];
   const int cdt = level_dt(c, cfg, lev + 1);
   void* bc = work(C, cdt, 2);
-  launch_resid_restrict(L, dt, bl, cur, bc, cdt, s);
-  launched("resid_restrict");
+  LAUNCH(c, HMG_K_RESID_RESTRICT, lev, s, launch_resid_restrict(L, dt, bl, cur, bc, cdt, s));
   void* ec = cdt == HMG_FP64 ? (void*)C.ux64 : (void*)C.ux32;
   cycle(c, cfg, lev + 1, bc, cdt, ec, cdt, s);
   // post-smoothing; the coarse correction is prolonged into the first sweep
   // (FP32) or added by its own pass first (FP64: fewer FP64 operations).
   const void* ec_in = ec;
   if (dt == HMG_FP64) {
-    launch_prolong(L, dt, cur, ec, cdt, s);
-    launched("prolong");
+    LAUNCH(c, HMG_K_PROLONG, lev, s, launch_prolong(L, dt, cur, ec, cdt, s));
     ec_in = nullptr;
   }
   for (int i = 0; i < cfg.nu_post; ++i) {
     bool last = i == cfg.nu_post - 1;
-    launch_sweep(L, dt, bl, cur, last ? out : nxt, last ? out_dt : dt, L.y32, i == 0 ? ec_in : nullptr, cdt,
-                 cfg.omega, s);
-    launched("sweep");
+    LAUNCH(c, HMG_K_SWEEP, lev, s,
+           launch_sweep(L, dt, bl, cur, last ? out : nxt, last ? out_dt : dt, i == 0 ? ec_in : nullptr, cdt,
+                        cfg.omega, last ? dot : nullptr, s));
     std::swap(cur, nxt);
   }
 }
@@ -174,6 +219,79 @@ Reduce red_with(const hmg_ctx* c, int epi, int slot = 0) {
   return r;
 }
 
+// One Krylov iteration after the first: z = V r, beta (device), p = z + beta p,
+// q = H^ p with alpha (device), x += alpha p, r -= alpha q with r.r, and the
+// scalars copied to page-locked host memory.
+// The dots r.z (and z.q) that form beta are fused into the last sweep of the
+// V-cycle when it has one (nu_post >= 1 always, so it does).
+SweepDot beta_dot(const hmg_ctx* c, bool flexible) {
+  SweepDot d;
+  d.a = c->kr;
+  d.c = flexible ? c->kq : nullptr;
+  d.red = red_with(c, flexible ? EPI_BETA_FCG : EPI_BETA_CG);
+  return d;
+}
+
+void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
+  Level& L = c->lv[0];
+  if (c->lv.size() > 1 || cfg.n_coarse > 1) {
+    SweepDot d = beta_dot(c, flexible);
+    cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s, &d);
+  } else {
+    cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
+    LAUNCH(c, HMG_K_DOT, 0, s,
+           launch_dot(L, c->kr, c->kz, flexible ? c->kz : nullptr, c->kq,
+                      red_with(c, flexible ? EPI_BETA_FCG : EPI_BETA_CG), s));
+  }
+  LAUNCH(c, HMG_K_UPDATE_P, 0, s, launch_update_p(L, c->kp, c->kz, c->red.sc, s));
+  Reduce ra = red_with(c, EPI_ALPHA);
+  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s));
+  LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
+  cuda_ok(cudaMemcpyAsync(c->host_sc, c->red.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s),
+          "scalar read");
+}
+
+int graph_key(const CycleCfg& cfg, bool flexible) {
+  return ((((cfg.mixed ? 1 : 0) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 + cfg.nu_post) * 65 + cfg.n_coarse;
+}
+
+// Replay (capturing it the first time) the iteration body as a CUDA graph.
+void run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
+  if (c->prof_on) {  // traced runs launch directly so that every kernel gets its events
+    iteration_body(c, cfg, flexible, s);
+    return;
+  }
+  const int key = graph_key(cfg, flexible);
+  hmg_ctx::BodyGraph* g = nullptr;
+  for (auto& bg : c->graphs)
+    if (bg.key == key) g = &bg;
+  if (!g) {
+    cudaGraph_t graph = nullptr;
+    const int64_t before = c->launches;
+    cudaStream_t cs = c->capture_stream;
+    cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+      iteration_body(c, cfg, flexible, cs);
+    } catch (...) {
+      cudaStreamEndCapture(cs, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    cuda_ok(cudaStreamEndCapture(cs, &graph), "end capture");
+    hmg_ctx::BodyGraph bg;
+    bg.key = key;
+    bg.kernels = (int)(c->launches - before);
+    c->launches = before;
+    cudaError_t e = cudaGraphInstantiate(&bg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cuda_ok(e, "graph instantiate");
+    c->graphs.push_back(bg);
+    g = &c->graphs.back();
+  }
+  cuda_ok(cudaGraphLaunch(g->exec, s), "graph launch");
+  c->launches += g->kernels;
+}
+
 hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
   Level& L = c->lv[0];
   CycleCfg cfg;
@@ -190,8 +308,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   cuda_ok(cudaMemsetAsync(c->red.sc, 0, S_COUNT * sizeof(double), s), "memset");
   cuda_ok(cudaMemsetAsync(c->kx, 0, bytes, s), "memset");
   cuda_ok(cudaMemcpyAsync(c->kr, c->kb, bytes, cudaMemcpyDeviceToDevice, s), "copy");
-  launch_dot(L, c->kr, c->kr, nullptr, nullptr, red_with(c, EPI_STORE0, S_BB), s);
-  launched("dot");
+  LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, c->kr, c->kr, nullptr, nullptr, red_with(c, EPI_STORE0, S_BB), s));
   read_scalars(c, s);
   const double bb = c->host_sc[S_BB];
   if (((int)c->host_sc[S_FLAG] & F_NONFINITE) || !std::isfinite(bb)) {
@@ -203,21 +320,26 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     inf.converged = 1;
     st = HMG_OK;
   } else {
-    cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
-    launch_dot(L, c->kr, c->kz, nullptr, nullptr, red_with(c, EPI_INIT_RZ), s);
-    launched("dot");
+    // first iteration: p = z = V r
+    if (c->lv.size() > 1 || cfg.n_coarse > 1) {
+      SweepDot d;
+      d.a = c->kr;
+      d.red = red_with(c, EPI_INIT_RZ);
+      cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s, &d);
+    } else {
+      cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
+      LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, c->kr, c->kz, nullptr, nullptr, red_with(c, EPI_INIT_RZ), s));
+    }
     cuda_ok(cudaMemcpyAsync(c->kp, c->kz, bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    Reduce ra = red_with(c, EPI_ALPHA);
+    LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s));
+    LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
+    read_scalars(c, s);
     const double stop2 = p.rtol * p.rtol * bb;
-    for (int k = 1; k <= p.max_iter; ++k) {
-      Reduce ra = red_with(c, EPI_ALPHA);
-      launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s);
-      launched("apply");
-      launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s);
-      launched("update_xr");
-      read_scalars(c, s);
+    for (int k = 1;; ++k) {
       inf.iterations = k;
-      int flag = (int)c->host_sc[S_FLAG];
-      double rr = c->host_sc[S_RR];
+      const int flag = (int)c->host_sc[S_FLAG];
+      const double rr = c->host_sc[S_RR];
       inf.rel_residual = std::sqrt(rr / bb);
       if (flag & F_NONFINITE) {
         st = HMG_ERR_NONFINITE;
@@ -233,19 +355,13 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
         break;
       }
       if (k == p.max_iter) break;
-      cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
-      launch_dot(L, c->kr, c->kz, flexible ? c->kz : nullptr, c->kq,
-                 red_with(c, flexible ? EPI_BETA_FCG : EPI_BETA_CG), s);
-      launched("dot");
-      launch_update_p(L, c->kp, c->kz, c->red.sc, s);
-      launched("update_p");
+      run_body(c, cfg, flexible, s);
+      cuda_ok(cudaStreamSynchronize(s), "solve");
     }
   }
   // true residual ||b - H^ x|| / ||b||
-  launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s);
-  launched("apply");
-  launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s);
-  launched("resid_sq");
+  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s));
+  LAUNCH(c, HMG_K_RESID_SQ, 0, s, launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s));
   cuda_ok(cudaEventRecord(c->ev1, s), "event");
   read_scalars(c, s);
   inf.true_rel_residual = bb > 0 ? std::sqrt(c->host_sc[S_TRUE] / bb) : 0.0;
@@ -301,7 +417,7 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
   hmg_status st = guarded(nullptr, [&] {
     require(p != nullptr, "params is NULL");
     require(p->refinement >= 0 && p->refinement <= 10, "refinement must be in [0, 10]");
-    require(p->nlayers >= 1 && p->nlayers <= 1024, "nlayers must be in [1, 1024]");
+    require(p->nlayers >= 1 && p->nlayers <= 256, "nlayers must be in [1, 256]");
     require(p->nlevels >= 1 && p->nlevels <= p->refinement + 1, "nlevels must be in [1, refinement + 1]");
     require(p->radius_m > 0 && std::isfinite(p->radius_m), "radius_m must be positive");
     require(p->thickness_m > 0 && std::isfinite(p->thickness_m), "thickness_m must be positive");
@@ -352,7 +468,6 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
       L.ua32 = dalloc<float>(c, L.Np);
       L.ub32 = dalloc<float>(c, L.Np);
       L.ux32 = dalloc<float>(c, L.Np);
-      L.y32 = dalloc<float>(c, L.Np);
     }
     const int64_t Np0 = c->lv[0].Np;
     c->kx = dalloc<double>(c, Np0);
@@ -369,6 +484,7 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
     cuda_ok(cudaHostAlloc((void**)&c->host_sc, S_COUNT * sizeof(double), cudaHostAllocDefault), "host alloc");
     cuda_ok(cudaEventCreate(&c->ev0), "event");
     cuda_ok(cudaEventCreate(&c->ev1), "event");
+    cuda_ok(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "stream");
     cuda_ok(cudaDeviceSynchronize(), "build");
   });
   if (st != HMG_OK) {
@@ -433,27 +549,21 @@ hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const do
     ph.omega = p->omega;
     ctx->has_theta = theta != nullptr;
     if (theta) {
-      launch_to_tiled(ctx->lv[0], HMG_FP64, theta, ctx->lv[0].theta, s);
-      launched("theta");
-      for (size_t k = 1; k < ctx->lv.size(); ++k) {
-        launch_theta_restrict(ctx->lv[k - 1], ctx->lv[k], s);
-        launched("theta_restrict");
-      }
+      LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(ctx->lv[0], HMG_FP64, theta, ctx->lv[0].theta, s));
+      for (size_t k = 1; k < ctx->lv.size(); ++k)
+        LAUNCH(ctx, HMG_K_ASSEMBLY, (int)k, s, launch_theta_restrict(ctx->lv[k - 1], ctx->lv[k], s));
     }
-    for (Level& L : ctx->lv) {
+    for (size_t k = 0; k < ctx->lv.size(); ++k) {
+      Level& L = ctx->lv[k];
+      const int lev = (int)k;
       double* th = L.theta;
       if (!theta) L.theta = nullptr;  // bands use theta = 1
-      launch_geometry(L, s);
-      launched("geometry");
-      launch_couplings(L, ph.wc2 * ph.dz, s);
-      launched("couplings");
-      launch_bands(L, ph, s);
-      launched("bands");
+      LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_geometry(L, s));
+      LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_couplings(L, ph.wc2 * ph.dz, s));
+      LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_bands(L, ph, s));
       L.theta = th;
-      launch_ldl(L, ph.omega, s);
-      launched("ldl");
-      launch_to_fp32(L, s);
-      launched("to_fp32");
+      LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_ldl(L, ph.omega, s));
+      LAUNCHN(ctx, HMG_K_ASSEMBLY, lev, s, 5, launch_to_fp32(L, s));
     }
     cuda_ok(cudaStreamSynchronize(s), "assemble");
     ctx->assembled = true;
@@ -471,16 +581,12 @@ hmg_status hmg_apply(hmg_ctx* ctx, int level, int dtype, int layout, const void*
     cudaStream_t s = as_stream(stream);
     Level& L = ctx->lv[level];
     if (layout == HMG_LAYOUT_TILED) {
-      launch_apply(L, dtype, x, y, nullptr, s);
-      launched("apply");
+      LAUNCH(ctx, HMG_K_APPLY, level, s, launch_apply(L, dtype, x, y, nullptr, s));
       return;
     }
-    launch_to_tiled(L, dtype, x, ctx->kcol, s);
-    launched("to_tiled");
-    launch_apply(L, dtype, ctx->kcol, ctx->kcol2, nullptr, s);
-    launched("apply");
-    launch_to_column(L, dtype, ctx->kcol2, y, s);
-    launched("to_column");
+    LAUNCH(ctx, HMG_K_LAYOUT, level, s, launch_to_tiled(L, dtype, x, ctx->kcol, s));
+    LAUNCH(ctx, HMG_K_APPLY, level, s, launch_apply(L, dtype, ctx->kcol, ctx->kcol2, nullptr, s));
+    LAUNCH(ctx, HMG_K_LAYOUT, level, s, launch_to_column(L, dtype, ctx->kcol2, y, s));
   });
 }
 
@@ -505,11 +611,9 @@ hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r, vo
       cycle(ctx, cfg, 0, r, HMG_FP64, z, HMG_FP64, s);
       return;
     }
-    launch_to_tiled(L, HMG_FP64, r, ctx->kcol, s);
-    launched("to_tiled");
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(L, HMG_FP64, r, ctx->kcol, s));
     cycle(ctx, cfg, 0, ctx->kcol, HMG_FP64, ctx->kcol2, HMG_FP64, s);
-    launch_to_column(L, HMG_FP64, ctx->kcol2, z, s);
-    launched("to_column");
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_column(L, HMG_FP64, ctx->kcol2, z, s));
   });
 }
 
@@ -523,11 +627,9 @@ hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_p
     need_assembled(ctx);
     cudaStream_t s = as_stream(stream);
     Level& L = ctx->lv[0];
-    launch_to_tiled(L, HMG_FP64, b, ctx->kb, s);
-    launched("to_tiled");
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(L, HMG_FP64, b, ctx->kb, s));
     result = solve_tiled(ctx, *params, info, s);
-    launch_to_column(L, HMG_FP64, ctx->kx, x, s);
-    launched("to_column");
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_column(L, HMG_FP64, ctx->kx, x, s));
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
   if (st != HMG_OK) return st;
@@ -548,11 +650,9 @@ hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host, co
     cudaStream_t s = as_stream(stream);
     Level& L = ctx->lv[0];
     cuda_ok(cudaMemcpyAsync(ctx->kcol, b_host, (size_t)L.N * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
-    launch_to_tiled(L, HMG_FP64, ctx->kcol, ctx->kb, s);
-    launched("to_tiled");
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(L, HMG_FP64, ctx->kcol, ctx->kb, s));
     result = solve_tiled(ctx, *params, info, s);
-    launch_to_column(L, HMG_FP64, ctx->kx, ctx->kcol, s);
-    launched("to_column");
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_column(L, HMG_FP64, ctx->kx, ctx->kcol, s));
     cuda_ok(cudaMemcpyAsync(x_host, ctx->kcol, (size_t)L.N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
@@ -568,9 +668,8 @@ hmg_status hmg_theta_grad(hmg_ctx* ctx, const double* p, const double* lambda, d
     Level& L = ctx->lv[0];
     double* th = L.theta;
     if (!ctx->has_theta) L.theta = nullptr;
-    launch_theta_grad(L, ctx->ph, p, lambda, grad, as_stream(stream));
+    LAUNCH(ctx, HMG_K_THETA_GRAD, 0, as_stream(stream), launch_theta_grad(L, ctx->ph, p, lambda, grad, as_stream(stream)));
     L.theta = th;
-    launched("theta_grad");
   });
 }
 
@@ -584,10 +683,63 @@ hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* 
                 (src_layout == HMG_LAYOUT_TILED && dst_layout == HMG_LAYOUT_COLUMN),
             "layouts must differ");
     Level& L = ctx->lv[level];
-    if (src_layout == HMG_LAYOUT_COLUMN) launch_to_tiled(L, HMG_FP64, src, dst, as_stream(stream));
-    else launch_to_column(L, HMG_FP64, src, dst, as_stream(stream));
-    launched("layout");
+    if (src_layout == HMG_LAYOUT_COLUMN)
+      LAUNCH(ctx, HMG_K_LAYOUT, level, as_stream(stream), launch_to_tiled(L, HMG_FP64, src, dst, as_stream(stream)));
+    else
+      LAUNCH(ctx, HMG_K_LAYOUT, level, as_stream(stream), launch_to_column(L, HMG_FP64, src, dst, as_stream(stream)));
   });
+}
+
+const char* hmg_kernel_name(int kernel) {
+  static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",   "prolong",  "resid_restrict",
+                                           "apply",  "dot",     "update_xr", "update_p",
+                                           "layout", "resid_sq", "assembly", "theta_grad"};
+  return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
+}
+
+hmg_status hmg_profile_start(hmg_ctx* ctx, unsigned kernel_mask, unsigned level_mask) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    ctx->prof.clear();
+    ctx->ev_used = 0;
+    ctx->prof_kmask = kernel_mask;
+    ctx->prof_lmask = level_mask;
+    ctx->prof_on = true;
+  });
+}
+
+hmg_status hmg_profile_stop(hmg_ctx* ctx, hmg_kernel_stat* out, int capacity, int* count) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    if (!ctx->prof_on) throw Fail{HMG_ERR_STATE, "tracing was not started"};
+    ctx->prof_on = false;
+    std::vector<hmg_kernel_stat> agg;
+    for (const ProfRec& r : ctx->prof) {
+      cudaEvent_t a = ctx->ev_pool[r.ev], b = ctx->ev_pool[r.ev + 1];
+      cuda_ok(cudaEventSynchronize(b), "event sync");
+      float ms = 0.f;
+      cuda_ok(cudaEventElapsedTime(&ms, a, b), "event time");
+      hmg_kernel_stat* hit = nullptr;
+      for (auto& st : agg)
+        if (st.kernel == r.kernel && st.level == r.level) hit = &st;
+      if (!hit) {
+        agg.push_back(hmg_kernel_stat{r.kernel, r.level, 0, 0.0});
+        hit = &agg.back();
+      }
+      hit->launches += 1;
+      hit->total_ms += ms;
+    }
+    ctx->prof.clear();
+    ctx->ev_used = 0;
+    if (count) *count = (int)agg.size();
+    for (int i = 0; out && i < capacity && i < (int)agg.size(); ++i) out[i] = agg[i];
+  });
+}
+
+hmg_status hmg_launch_count(const hmg_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return HMG_ERR_INVALID_ARG;
+  *count = ctx->launches;
+  return HMG_OK;
 }
 
 hmg_status hmg_sync(hmg_ctx* ctx, void* stream) {

@@ -24,7 +24,7 @@
 namespace hmg {
 
 constexpr int TW = 32;                 // columns per tile
-constexpr int RED_MAX_BLOCKS = 2048;   // partial sums of one reduction
+constexpr int RED_MAX_BLOCKS = 16384;  // partial sums of one reduction (>= tiles of the finest level)
 
 struct HostLevel {
   int refinement = 0;
@@ -56,7 +56,7 @@ struct Level {
   // b: right-hand side of this level (restricted residual); ua, ub: smoother
   // ping-pong; ux: result of this level's cycle (the coarse correction)
   double *b64 = nullptr, *ua64 = nullptr, *ub64 = nullptr, *ux64 = nullptr;
-  float *b32 = nullptr, *ua32 = nullptr, *ub32 = nullptr, *ux32 = nullptr, *y32 = nullptr;
+  float *b32 = nullptr, *ua32 = nullptr, *ub32 = nullptr, *ux32 = nullptr;
 };
 
 // Slots of the Krylov scalars kept on the device.
@@ -101,8 +101,14 @@ void launch_theta_grad(const Level& L, const Phys& ph, const double* p_col, cons
 // each void* buffer.
 void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, float* bcopy,
                    double omega, cudaStream_t s);
-void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo, int uo_dt,
-                  void* ytmp, const void* ec, int ec_dt, double omega, cudaStream_t s);
+// Optional dot products fused into a sweep: s0 = a . u', s1 = u' . c (c may be null).
+struct SweepDot {
+  const double* a = nullptr;
+  const double* c = nullptr;
+  Reduce red{};
+};
+void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo, int uo_dt, const void* ec,
+                  int ec_dt, double omega, const SweepDot* dot, cudaStream_t s);
 void launch_prolong(const Level& L, int dt, void* u, const void* ec, int ec_dt, cudaStream_t s);
 void launch_resid_restrict(const Level& L, int dt, const void* b, const void* u, void* bc, int bc_dt,
                            cudaStream_t s);
@@ -124,6 +130,13 @@ int reduce_grid(int64_t n);
 
 }  // namespace hmg
 
+namespace hmg {
+struct ProfRec {
+  int kernel, level;
+  size_t ev;  // index of the start event in the pool; the end event follows
+};
+}  // namespace hmg
+
 struct hmg_ctx {
   hmg_mesh_params mp{};
   hmg_op_params op{};
@@ -139,4 +152,19 @@ struct hmg_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void*> allocations;
   std::string err;
+  // tracing
+  bool prof_on = false;
+  unsigned prof_kmask = 0, prof_lmask = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<hmg::ProfRec> prof;
+  int64_t launches = 0;
+  // CUDA graphs of the Krylov iteration body, one per cycle configuration
+  struct BodyGraph {
+    int key = -1;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+  };
+  std::vector<BodyGraph> graphs;
+  cudaStream_t capture_stream = nullptr;  // graphs are captured here, launched on the caller's stream
 };
