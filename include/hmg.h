@@ -181,6 +181,30 @@ hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* 
 /* Synchronise `stream` and report any pending device error. */
 hmg_status hmg_sync(hmg_ctx* ctx, void* stream);
 
+/* Largest level (padded TILED length, ncells_padded) hmg_apply_noalloc accepts. */
+#define HMG_NOALLOC_MAX_CELLS 524288
+
+/* hmg_apply with COLUMN-layout FP64 vectors, for callers that may not
+ * allocate device memory at the point of the call: code running while another
+ * component captures a CUDA graph (an allocation there is either refused or
+ * becomes part of the graph), code inside a framework that owns the whole
+ * device memory pool and forbids side allocations, and latency-bound loops
+ * where cudaMalloc / cudaFree would synchronise the device.  The paper has no
+ * counterpart: this is an interface convenience, not part of the method.
+ * y = H^ x on `level`, the same result as hmg_apply(ctx, level, HMG_FP64,
+ * HMG_LAYOUT_COLUMN, x, y, stream).  The two staging vectors that hmg_apply
+ * takes from the context live instead in one fixed array of
+ * 2 * HMG_NOALLOC_MAX_CELLS doubles (8 MiB) inside the library, which every
+ * device that loads the library keeps until the process exits; the call
+ * allocates nothing.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU (other streams, other threads) race and must be ordered by the
+ * caller.  Each call overwrites every staging entry it reads.  Errors:
+ * INVALID_ARG (bad level or pointers, or ncells_padded of the level above
+ * HMG_NOALLOC_MAX_CELLS), STATE (not assembled), CUDA. */
+hmg_status hmg_apply_noalloc(hmg_ctx* ctx, int level, const double* x, double* y, void* stream);
+
 /* Kernel classes reported by the tracing calls below. */
 typedef enum {
   HMG_K_SWEEP0 = 0,          /* first line relaxation from u = 0 */

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "hmg_export_mesh": [_P, _I, _P, _P],
     "hmg_assemble_helmholtz": [_P, ctypes.POINTER(OpParams), _P, _P],
     "hmg_apply": [_P, _I, _I, _I, _P, _P, _P],
+    "hmg_apply_noalloc": [_P, _I, _P, _P, _P],
     "hmg_vcycle": [_P, _I, _I, _P, _P, _I, _I, _I, _P],
     "hmg_solve": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
     "hmg_solve_host": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
@@ -198,6 +199,16 @@ class Hierarchy:
         x = x.contiguous()
         y = out if out is not None else torch.empty_like(x)
         self._check(self.lib.hmg_apply(self._ctx, level, dtype, LAYOUT[layout], _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def apply_noalloc(self, x, level=0, out=None, stream=None):
+        """y = H^ x (FP64, COLUMN layout) through hmg_apply_noalloc: no device
+        memory is allocated by the library for the call (out must be given to
+        avoid the allocation of the result tensor here)."""
+        assert x.is_cuda and x.dtype == torch.float64 and x.numel() == self._len(level, "column")
+        x = x.contiguous()
+        y = out if out is not None else torch.empty_like(x)
+        self._check(self.lib.hmg_apply_noalloc(self._ctx, level, _ptr(x), _ptr(y), _stream(stream)))
         return y
 
     def vcycle(self, r, precision="fp64", layout="column", nu_pre=2, nu_post=2, n_coarse=2, out=None, stream=None):
