@@ -565,7 +565,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--oracle-iterations", type=int, default=2)
+    ap.add_argument("--oracle-iterations", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)

@@ -44,6 +44,14 @@ T* dalloc(hmg_ctx* c, size_t count) {
   return static_cast<T*>(p);
 }
 
+void destroy_graph_prof(std::vector<GraphProf>& v) {
+  for (auto& gp : v) {
+    if (gp.a) cudaEventDestroy(gp.a);
+    if (gp.b) cudaEventDestroy(gp.b);
+  }
+  v.clear();
+}
+
 void release(hmg_ctx* c) {
   for (void* p : c->allocations) cudaFree(p);
   c->allocations.clear();
@@ -54,8 +62,10 @@ void release(hmg_ctx* c) {
   c->ev0 = c->ev1 = nullptr;
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
-  for (auto& g : c->graphs)
+  for (auto& g : c->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
+    destroy_graph_prof(g.prof);
+  }
   c->graphs.clear();
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   c->capture_stream = nullptr;
@@ -97,10 +107,20 @@ cudaEvent_t pool_event(hmg_ctx* c) {
   return c->ev_pool[c->ev_used++];
 }
 
+// Returns -1 (not traced), a record index >= 0 (direct launch), or
+// -2 - i for event pair i of the graph being captured.
 int prof_begin(hmg_ctx* c, int kernel, int level, cudaStream_t s) {
   if (!c->prof_on || !((c->prof_kmask >> kernel) & 1u) || level < 0 || level > 31 ||
       !((c->prof_lmask >> level) & 1u))
     return -1;
+  if (c->capturing) {
+    GraphProf gp{kernel, level, nullptr, nullptr};
+    cuda_ok(cudaEventCreate(&gp.a), "event");
+    cuda_ok(cudaEventCreate(&gp.b), "event");
+    c->capture_prof.push_back(gp);
+    cuda_ok(cudaEventRecordWithFlags(gp.a, s, cudaEventRecordExternal), "event");
+    return -2 - ((int)c->capture_prof.size() - 1);
+  }
   size_t idx = c->ev_used;
   cudaEvent_t a = pool_event(c);
   pool_event(c);
@@ -110,8 +130,22 @@ int prof_begin(hmg_ctx* c, int kernel, int level, cudaStream_t s) {
 }
 
 void prof_end(hmg_ctx* c, int rec, cudaStream_t s) {
-  if (rec < 0) return;
+  if (rec == -1) return;
+  if (rec <= -2) {
+    cuda_ok(cudaEventRecordWithFlags(c->capture_prof[-2 - rec].b, s, cudaEventRecordExternal), "event");
+    return;
+  }
   cuda_ok(cudaEventRecord(c->ev_pool[c->prof[rec].ev + 1], s), "event");
+}
+
+void prof_add(hmg_ctx* c, int kernel, int level, double ms) {
+  for (auto& st : c->prof_agg)
+    if (st.kernel == kernel && st.level == level) {
+      st.launches += 1;
+      st.total_ms += ms;
+      return;
+    }
+  c->prof_agg.push_back(hmg_kernel_stat{kernel, level, 1, ms});
 }
 
 // Launch `call` (one or more kernels), check the launch, count it and, when
@@ -256,40 +290,59 @@ int graph_key(const CycleCfg& cfg, bool flexible) {
 }
 
 // Replay (capturing it the first time) the iteration body as a CUDA graph.
-void run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
-  if (c->prof_on) {  // traced runs launch directly so that every kernel gets its events
-    iteration_body(c, cfg, flexible, s);
-    return;
-  }
+// With tracing on, the graph carries event nodes around the traced kernels;
+// harvest_body() reads them after the replay has completed.
+hmg_ctx::BodyGraph* run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
   const int key = graph_key(cfg, flexible);
+  const unsigned long long trace =
+      c->prof_on ? (((unsigned long long)c->prof_kmask << 32) | c->prof_lmask) | (1ull << 63) : 0ull;
   hmg_ctx::BodyGraph* g = nullptr;
   for (auto& bg : c->graphs)
-    if (bg.key == key) g = &bg;
+    if (bg.key == key && bg.trace == trace) g = &bg;
   if (!g) {
     cudaGraph_t graph = nullptr;
     const int64_t before = c->launches;
     cudaStream_t cs = c->capture_stream;
+    c->capture_prof.clear();
     cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c->capturing = true;
     try {
       iteration_body(c, cfg, flexible, cs);
     } catch (...) {
+      c->capturing = false;
       cudaStreamEndCapture(cs, &graph);
       if (graph) cudaGraphDestroy(graph);
+      destroy_graph_prof(c->capture_prof);
       throw;
     }
+    c->capturing = false;
     cuda_ok(cudaStreamEndCapture(cs, &graph), "end capture");
     hmg_ctx::BodyGraph bg;
     bg.key = key;
+    bg.trace = trace;
     bg.kernels = (int)(c->launches - before);
+    bg.prof.swap(c->capture_prof);
     c->launches = before;
     cudaError_t e = cudaGraphInstantiate(&bg.exec, graph, 0);
     cudaGraphDestroy(graph);
+    if (e != cudaSuccess) destroy_graph_prof(bg.prof);
     cuda_ok(e, "graph instantiate");
-    c->graphs.push_back(bg);
+    c->graphs.push_back(std::move(bg));
     g = &c->graphs.back();
   }
   cuda_ok(cudaGraphLaunch(g->exec, s), "graph launch");
   c->launches += g->kernels;
+  return g;
+}
+
+// After the replay of g has completed: add its traced kernels to the records.
+void harvest_body(hmg_ctx* c, const hmg_ctx::BodyGraph* g) {
+  if (!c->prof_on || !g) return;
+  for (const GraphProf& gp : g->prof) {
+    float ms = 0.f;
+    cuda_ok(cudaEventElapsedTime(&ms, gp.a, gp.b), "event time");
+    prof_add(c, gp.kernel, gp.level, ms);
+  }
 }
 
 hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
@@ -355,8 +408,9 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
         break;
       }
       if (k == p.max_iter) break;
-      run_body(c, cfg, flexible, s);
+      hmg_ctx::BodyGraph* g = run_body(c, cfg, flexible, s);
       cuda_ok(cudaStreamSynchronize(s), "solve");
+      harvest_body(c, g);
     }
   }
   // true residual ||b - H^ x|| / ||b||
@@ -701,6 +755,7 @@ hmg_status hmg_profile_start(hmg_ctx* ctx, unsigned kernel_mask, unsigned level_
   if (!ctx) return HMG_ERR_INVALID_ARG;
   return guarded(ctx, [&] {
     ctx->prof.clear();
+    ctx->prof_agg.clear();
     ctx->ev_used = 0;
     ctx->prof_kmask = kernel_mask;
     ctx->prof_lmask = level_mask;
@@ -712,23 +767,16 @@ hmg_status hmg_profile_stop(hmg_ctx* ctx, hmg_kernel_stat* out, int capacity, in
   if (!ctx) return HMG_ERR_INVALID_ARG;
   return guarded(ctx, [&] {
     if (!ctx->prof_on) throw Fail{HMG_ERR_STATE, "tracing was not started"};
-    ctx->prof_on = false;
-    std::vector<hmg_kernel_stat> agg;
     for (const ProfRec& r : ctx->prof) {
       cudaEvent_t a = ctx->ev_pool[r.ev], b = ctx->ev_pool[r.ev + 1];
       cuda_ok(cudaEventSynchronize(b), "event sync");
       float ms = 0.f;
       cuda_ok(cudaEventElapsedTime(&ms, a, b), "event time");
-      hmg_kernel_stat* hit = nullptr;
-      for (auto& st : agg)
-        if (st.kernel == r.kernel && st.level == r.level) hit = &st;
-      if (!hit) {
-        agg.push_back(hmg_kernel_stat{r.kernel, r.level, 0, 0.0});
-        hit = &agg.back();
-      }
-      hit->launches += 1;
-      hit->total_ms += ms;
+      prof_add(ctx, r.kernel, r.level, ms);
     }
+    ctx->prof_on = false;
+    std::vector<hmg_kernel_stat> agg;
+    agg.swap(ctx->prof_agg);
     ctx->prof.clear();
     ctx->ev_used = 0;
     if (count) *count = (int)agg.size();

@@ -125,7 +125,11 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
       const int l = l0 + i * NW;
       if (l < nz) {
         T r = bl[i];
-        if (MODE != MODE_ZERO) r += g.x * a0[i] + g.y * a1[i] + g.z * a2[i];
+        if (MODE != MODE_ZERO) {  // three FMAs: b + g0 u0 + g1 u1 + g2 u2
+          r = fma(g.x, a0[i], r);
+          r = fma(g.y, a1[i], r);
+          r = fma(g.z, a2[i], r);
+        }
         if (bcopy && valid) bcopy[base + (int64_t)l * TW] = (float)bl[i];
         R[l * TW + lane] = r;
         LOs[l * TW + lane] = lo[i];
@@ -264,17 +268,19 @@ k_tprolong(int nc, int nz, int ntiles, int RG, T* __restrict__ u, const TE* __re
   }
 }
 
-// (H^ x) at (column c, layer l) = tiled index t
-template <typename T>
-__device__ __forceinline__ T stencil_at(const LD<T>& L, const T* __restrict__ x, int64_t t, int l,
-                                        const typename Vec4<T>::type& g, int64_t s0, int64_t s1, int64_t s2) {
+// acc + sgn (H^ x) at (column c, layer l) = tiled index t, as one FMA chain:
+// sgn = +1 gives H^ x (acc = 0: one MUL and five FMAs), sgn = -1 with acc = b
+// gives the residual b - H^ x in six FMAs.
+template <typename T, int SGN>
+__device__ __forceinline__ T stencil_acc(const LD<T>& L, const T* __restrict__ x, int64_t t, int l, T acc,
+                                         const typename Vec4<T>::type& g, int64_t s0, int64_t s1, int64_t s2) {
   const int64_t o = (int64_t)l * TW;
-  T y = L.d[t] * x[t];
-  if (l > 0) y += L.e[t] * x[t - TW];
-  if (l < L.nz - 1) y += L.e[t + TW] * x[t + TW];
-  y -= g.x * x[s0 + o];
-  y -= g.y * x[s1 + o];
-  y -= g.z * x[s2 + o];
+  T y = (SGN > 0) ? L.d[t] * x[t] : fma(-L.d[t], x[t], acc);
+  if (l > 0) y = fma((T)SGN * L.e[t], x[t - TW], y);
+  if (l < L.nz - 1) y = fma((T)SGN * L.e[t + TW], x[t + TW], y);
+  y = fma((T)(-SGN) * g.x, x[s0 + o], y);
+  y = fma((T)(-SGN) * g.y, x[s1 + o], y);
+  y = fma((T)(-SGN) * g.z, x[s2 + o], y);
   return y;
 }
 
@@ -305,7 +311,7 @@ k_tresid_restrict(LD<T> L, int ntiles, int RG, const T* __restrict__ b, const T*
     for (int l = row0; l < nz; l += rstep) {
       const int64_t t = base + (int64_t)l * TW;
       T r = 0;
-      if (valid) r = b[t] - stencil_at(L, u, t, l, g, s0, s1, s2);
+      if (valid) r = stencil_acc<T, -1>(L, u, t, l, b[t], g, s0, s1, s2);
       r += __shfl_xor_sync(0xffffffffu, r, 1);
       r += __shfl_xor_sync(0xffffffffu, r, 2);
       if ((lane & 3) == 0 && valid) bc[qc + (int64_t)l * TW] = (TC)r;
@@ -338,7 +344,7 @@ k_tapply(LD<T> L, int ntiles, int RG, const T* __restrict__ x, T* __restrict__ y
     for (int l = row0; l < nz; l += rstep) {
       const int64_t t = base + (int64_t)l * TW;
       T v = 0;
-      if (valid) v = stencil_at(L, x, t, l, g, s0, s1, s2);
+      if (valid) v = stencil_acc<T, 1>(L, x, t, l, (T)0, g, s0, s1, s2);
       y[t] = v;
       if (DOT) acc += (double)x[t] * (double)v;
     }

@@ -135,6 +135,11 @@ struct ProfRec {
   int kernel, level;
   size_t ev;  // index of the start event in the pool; the end event follows
 };
+// Events recorded as nodes of a captured graph (re-recorded at every replay).
+struct GraphProf {
+  int kernel, level;
+  cudaEvent_t a, b;
+};
 }  // namespace hmg
 
 struct hmg_ctx {
@@ -158,12 +163,17 @@ struct hmg_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<hmg::ProfRec> prof;
+  std::vector<hmg_kernel_stat> prof_agg;          // accumulated records
+  bool capturing = false;
+  std::vector<hmg::GraphProf> capture_prof;       // events of the graph being captured
   int64_t launches = 0;
   // CUDA graphs of the Krylov iteration body, one per cycle configuration
   struct BodyGraph {
     int key = -1;
+    unsigned long long trace = 0;   // tracing masks the graph was captured with (0: none)
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;
+    std::vector<hmg::GraphProf> prof;
   };
   std::vector<BodyGraph> graphs;
   cudaStream_t capture_stream = nullptr;  // graphs are captured here, launched on the caller's stream

@@ -1,0 +1,149 @@
+"""Parity at the full workload sizes, in the configuration bench.py times.
+
+r6x64 (81,920 columns x 64 layers, 5 levels): whole-vector operator and
+V-cycle parity, the FP64 solve against the oracle's solve (iteration count
+within 1; it is also the count bench.py uses to scale the oracle sample), a
+manufactured solution and the mixed form's error.  r5x64 with theta:
+adjoint gradients against the oracle and central differences in 32 seeded
+directions.  r7x128 (42M cells): the oracle cannot solve it in seconds, so
+properties that hold at any size are checked (row sums = cell volumes from
+the oracle's mesh, symmetry, converged true residuals, both forms agree).
+"""
+import numpy as np
+import pytest
+
+import bench
+import hmg_inputs as gi
+from oracle import adjoint, helmholtz, krylov, mesh, multigrid
+from tests.helpers import cell_permutation, column_permutation, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1605_00492_gb300 as hmg  # noqa: E402
+
+DEV = "cuda:0"
+
+
+class Full:
+    def __init__(self, name, theta=False):
+        w = gi.WORKLOADS[name]
+        self.r, self.nz, self.L = w["refinement"], w["nlayers"], w["nlevels"]
+        self.ms = mesh.hierarchy(self.r, self.L)
+        self.prm = helmholtz.Params(refinement=self.r, nlayers=self.nz)
+        n = self.ms[0].ncols * self.nz
+        self.theta = gi.theta(n) if theta else None
+        self.ops = helmholtz.assemble_hierarchy(self.ms, self.prm, self.theta)
+        self.h = hmg.Hierarchy(self.r, self.nz, self.L)
+        cen, _ = self.h.export_mesh(0)
+        self.idx = cell_permutation(column_permutation(cen, self.ms[0].centroid), self.nz)
+        self.h.assemble(theta=self.gpu(self.theta) if theta else None)
+
+    def gpu(self, v):
+        return torch.tensor(np.asarray(v)[self.idx], dtype=torch.float64, device=DEV)
+
+    @staticmethod
+    def host(t):
+        return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def r6():
+    f = Full("r6x64")
+    yield f
+    f.h.close()
+
+
+def test_r6x64_apply_and_vcycle(r6):
+    x = gi.rhs(r6.ops[0].ncells, seed=7)
+    y = r6.h.apply(r6.gpu(x))
+    assert rel_l2(r6.host(y), (r6.ops[0].H @ x)[r6.idx]) < 1e-13
+    b = gi.rhs(r6.ops[0].ncells)
+    z_ref = multigrid.vcycle(r6.ops, b)
+    z = r6.h.vcycle(r6.gpu(b))
+    assert rel_l2(r6.host(z), z_ref[r6.idx]) < 1e-12
+    zm = r6.h.vcycle(r6.gpu(b), precision="mixed")
+    assert rel_l2(r6.host(zm), z_ref[r6.idx]) < 1e-4
+
+
+def test_r6x64_solve_matches_oracle(r6):
+    b = gi.rhs(r6.ops[0].ncells)
+    x_ref, info_ref = krylov.pcg(r6.ops[0].H.dot, lambda v: multigrid.vcycle(r6.ops, v), b, rtol=1e-8)
+    x, info = r6.h.solve(r6.gpu(b), rtol=1e-8)
+    assert info["converged"] == 1 and info["true_rel_residual"] < 2e-8
+    assert abs(info["iterations"] - info_ref.iterations) <= 1
+    assert info_ref.iterations == bench.ORACLE_ITERATIONS
+    assert rel_l2(r6.host(x), x_ref[r6.idx]) <= 1e-9
+    # mixed form: error against the FP64 oracle solution, stated here
+    xm, infom = r6.h.solve(r6.gpu(b), precision="mixed", rtol=1e-8)
+    assert infom["converged"] == 1 and infom["true_rel_residual"] < 2e-8
+    assert rel_l2(r6.host(xm), x_ref[r6.idx]) < 1e-6
+
+
+def test_r6x64_manufactured_solution(r6):
+    ps = gi.pstar(r6.ops[0].ncells)
+    b = r6.ops[0].H @ ps
+    x, info = r6.h.solve(r6.gpu(b), rtol=1e-10)
+    assert info["converged"] == 1
+    assert rel_l2(r6.host(x), ps[r6.idx]) < 1e-6
+
+
+def test_r5x64_adjoint_gradients():
+    f = Full("r5x64a", theta=True)
+    n = f.ops[0].ncells
+    kw = dict(rtol=1e-13, max_iter=400)
+    b = f.gpu(gi.rhs(n)).requires_grad_(True)
+    th = f.gpu(f.theta).requires_grad_(True)
+    p = hmg.HelmholtzSolve.apply(f.h, b, th, kw, kw)
+    pt = f.gpu(gi.ptarget(n)) * p.detach().abs().max()
+    loss = 0.5 * ((p - pt) ** 2).sum()
+    loss.backward()
+    solve = lambda ops, rhs: krylov.pcg(ops[0].H.dot, lambda v: multigrid.vcycle(ops, v), rhs, rtol=1e-13,
+                                        max_iter=400)[0]
+    pt_or = np.empty(n)
+    pt_or[f.idx] = f.host(pt)
+    L_ref, lam_ref, g_ref, _ = adjoint.value_and_grad(f.ops, f.prm, f.ms[0], f.theta, gi.rhs(n), pt_or, solve)
+    assert float(loss.detach()) == pytest.approx(L_ref, rel=1e-9)
+    assert rel_l2(f.host(b.grad), lam_ref[f.idx]) < 1e-8
+    assert rel_l2(f.host(th.grad), g_ref[f.idx]) < 1e-8
+    # central differences, h = 1e-6, 32 seeded directions
+    with torch.no_grad():
+        for v in gi.directions(n, 32):
+            vg = f.gpu(v)
+            Lp = 0.5 * ((hmg.HelmholtzSolve.apply(f.h, b, th + 1e-6 * vg, kw, kw) - pt) ** 2).sum()
+            Lm = 0.5 * ((hmg.HelmholtzSolve.apply(f.h, b, th - 1e-6 * vg, kw, kw) - pt) ** 2).sum()
+            fd = float(Lp - Lm) / 2e-6
+            assert float((th.grad * vg).sum()) == pytest.approx(fd, rel=1e-5)
+    f.h.close()
+
+
+def test_r7x128_properties_both_forms():
+    w = gi.WORKLOADS["r7x128"]
+    r, nz, L = w["refinement"], w["nlayers"], w["nlevels"]
+    m = mesh.hierarchy(r, 1)[0]
+    prm = helmholtz.Params(refinement=r, nlayers=nz)
+    vol = (m.area1[:, None] * prm.rho()[None, :] ** 2 * prm.dz).reshape(-1)
+    h = hmg.Hierarchy(r, nz, L)
+    h.assemble()
+    cen, _ = h.export_mesh(0)
+    idx = cell_permutation(column_permutation(cen, m.centroid), nz)
+    n = h.ncells
+    ones = torch.ones(n, dtype=torch.float64, device=DEV)
+    y = h.apply(ones).cpu().numpy()
+    # the diagonal (~1e16) cancels against the vertical couplings to ~1e11: rounding ~1e-10 relative
+    assert np.max(np.abs(y - vol[idx]) / vol[idx]) < 1e-8
+    x1 = torch.tensor(gi.rhs(n, seed=8), device=DEV)
+    x2 = torch.tensor(gi.rhs(n, seed=9), device=DEV)
+    a = float(torch.dot(x1, h.apply(x2)))
+    c = float(torch.dot(x2, h.apply(x1)))
+    assert a == pytest.approx(c, rel=1e-12)
+    b = torch.tensor(gi.rhs(n), device=DEV)
+    x64, i64 = h.solve(b, rtol=1e-8)
+    xm, im = h.solve(b, precision="mixed", rtol=1e-8)
+    assert i64["converged"] == 1 and im["converged"] == 1
+    assert i64["true_rel_residual"] < 2e-8 and im["true_rel_residual"] < 2e-8
+    assert float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)) < 1e-6
+    h.close()

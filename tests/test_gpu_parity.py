@@ -259,3 +259,23 @@ def test_autograd_against_oracle_and_finite_differences():
             Lm = 0.5 * ((hmg.HelmholtzSolve.apply(c.h, b, th - 1e-6 * vg, kw, kw) - pt) ** 2).sum()
             fd = float(Lp - Lm) / 2e-6
             assert float((th.grad * vg).sum()) == pytest.approx(fd, rel=1e-5)
+
+
+def test_tracing_counts_kernels_inside_graphs():
+    """Tracing (CUDA events around selected kernels) also works when the
+    iteration body runs as a CUDA graph; per V-cycle the finest level runs
+    one sweep0, nu_pre - 1 + nu_post sweeps and one residual+restriction."""
+    c = case(3, 16, 3)
+    b = c.gpu(gi.rhs(c.ops[0].ncells))
+    c.h.solve(b)                                   # captures the graph untraced
+    c.h.profile_start(kernels=["sweep", "sweep0", "resid_restrict"], levels=[0])
+    _, info = c.h.solve(b)
+    rec = c.h.profile_stop()
+    k = info["iterations"]
+    assert rec[("sweep", 0)][0] == 3 * k
+    assert rec[("sweep0", 0)][0] == k
+    assert rec[("resid_restrict", 0)][0] == k
+    assert all(ms > 0 for _, ms in rec.values())
+    n0 = c.h.launch_count()
+    c.h.solve(b)
+    assert c.h.launch_count() > n0
