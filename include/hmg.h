@@ -178,6 +178,14 @@ hmg_status hmg_theta_grad(hmg_ctx* ctx, const double* p, const double* lambda,
 hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* src,
                          int dst_layout, double* dst, void* stream);
 
+/* Element-wise conversions used by the mixed-precision cycle, done with
+ * integer operations on the bit patterns (on GB300 the hardware conversion
+ * issues on the slow FP64 pipe): FP64 -> FP32 rounds to nearest, ties to even
+ * (IEEE 754 roundTiesToEven); FP32 -> FP64 is exact.  n elements, device
+ * pointers, src and dst must not overlap.  Errors: INVALID_ARG, CUDA. */
+hmg_status hmg_convert_fp64_to_fp32(const double* src, float* dst, int64_t n, void* stream);
+hmg_status hmg_convert_fp32_to_fp64(const float* src, double* dst, int64_t n, void* stream);
+
 /* Synchronise `stream` and report any pending device error. */
 hmg_status hmg_sync(hmg_ctx* ctx, void* stream);
 

@@ -90,6 +90,8 @@ _SIGNATURES = {
     "hmg_theta_grad": [_P, _P, _P, _P, _P],
     "hmg_to_layout": [_P, _I, _I, _P, _I, _P, _P],
     "hmg_sync": [_P, _P],
+    "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
+    "hmg_convert_fp32_to_fp64": [_P, _P, ctypes.c_int64, _P],
     "hmg_profile_start": [_P, ctypes.c_uint, ctypes.c_uint],
     "hmg_profile_stop": [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)],
     "hmg_launch_count": [_P, ctypes.POINTER(ctypes.c_int64)],
@@ -285,6 +287,22 @@ class Hierarchy:
 
     def sync(self, stream=None):
         self._check(self.lib.hmg_sync(self._ctx, _stream(stream)))
+
+
+def convert(x, dtype, stream=None):
+    """FP64 <-> FP32 on the GPU with the library's integer-pipe conversion."""
+    lib = load_library()
+    assert x.is_cuda and x.is_contiguous()
+    out = torch.empty(x.shape, dtype=dtype, device=x.device)
+    if x.dtype == torch.float64 and dtype == torch.float32:
+        st = lib.hmg_convert_fp64_to_fp32(_ptr(x), _ptr(out), x.numel(), _stream(stream))
+    elif x.dtype == torch.float32 and dtype == torch.float64:
+        st = lib.hmg_convert_fp32_to_fp64(_ptr(x), _ptr(out), x.numel(), _stream(stream))
+    else:
+        raise ValueError("convert: FP64 -> FP32 or FP32 -> FP64 only")
+    if st != HMG_OK:
+        raise HMGError(st, "conversion failed")
+    return out
 
 
 from .autograd import HelmholtzSolve  # noqa: E402  (needs Hierarchy)

@@ -216,10 +216,13 @@ void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, vo
   LAUNCH(c, HMG_K_RESID_RESTRICT, lev, s, launch_resid_restrict(L, dt, bl, cur, bc, cdt, s));
   void* ec = cdt == HMG_FP64 ? (void*)C.ux64 : (void*)C.ux32;
   cycle(c, cfg, lev + 1, bc, cdt, ec, cdt, s);
-  // post-smoothing; the coarse correction is prolonged into the first sweep
-  // (FP32) or added by its own pass first (FP64: fewer FP64 operations).
+  // post-smoothing; the coarse correction is added by its own pass first on
+  // large FP64 levels (1 instead of 4 FP64 operations per cell) and on small
+  // FP32 levels (whose staged sweep takes no fused prolongation), and is
+  // prolonged inside the first sweep elsewhere.
   const void* ec_in = ec;
-  if (dt == HMG_FP64) {
+  const bool small = L.ncp / TW <= FUSED_PROLONG_MAX_TILES;
+  if ((dt == HMG_FP64 && !small) || (dt == HMG_FP32 && small)) {
     LAUNCH(c, HMG_K_PROLONG, lev, s, launch_prolong(L, dt, cur, ec, cdt, s));
     ec_in = nullptr;
   }
@@ -488,6 +491,9 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
       L.nz = p->nlayers;
       L.N = (int64_t)L.nc * L.nz;
       L.Np = (int64_t)L.ncp * L.nz;
+      // twisted two-chain column solves on the small (latency-bound) levels,
+      // the same tile threshold as the 16-warp sweep CTAs of cycle.cu
+      L.twist = (L.ncp / TW <= SMALL_LEVEL_TILES) ? L.nz / 2 : L.nz - 1;
       L.centroid_host = H.centroid;
       L.nbr_host = H.nbr;
       std::vector<int4> nb(L.ncp);
@@ -513,6 +519,8 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
       L.e32 = dalloc<float>(c, L.Np);
       L.lo32 = dalloc<float>(c, L.Np);
       L.w32 = dalloc<float>(c, L.Np);
+      L.mt = dalloc<double>(c, L.ncp);
+      L.mt32 = dalloc<float>(c, L.ncp);
       L.theta = dalloc<double>(c, L.Np);
       L.b64 = dalloc<double>(c, L.Np);
       L.ua64 = dalloc<double>(c, L.Np);
@@ -617,7 +625,7 @@ hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const do
       LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_bands(L, ph, s));
       L.theta = th;
       LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_ldl(L, ph.omega, s));
-      LAUNCHN(ctx, HMG_K_ASSEMBLY, lev, s, 5, launch_to_fp32(L, s));
+      LAUNCHN(ctx, HMG_K_ASSEMBLY, lev, s, 6, launch_to_fp32(L, s));
     }
     cuda_ok(cudaStreamSynchronize(s), "assemble");
     ctx->assembled = true;
@@ -745,9 +753,9 @@ hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* 
 }
 
 const char* hmg_kernel_name(int kernel) {
-  static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",   "prolong",  "resid_restrict",
-                                           "apply",  "dot",     "update_xr", "update_p",
-                                           "layout", "resid_sq", "assembly", "theta_grad"};
+  static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",     "prolong",  "resid_restrict", "apply",
+                                           "dot",    "update_xr", "update_p", "layout",         "resid_sq",
+                                           "assembly", "theta_grad"};
   return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
 }
 
@@ -788,6 +796,20 @@ hmg_status hmg_launch_count(const hmg_ctx* ctx, int64_t* count) {
   if (!ctx || !count) return HMG_ERR_INVALID_ARG;
   *count = ctx->launches;
   return HMG_OK;
+}
+
+hmg_status hmg_convert_fp64_to_fp32(const double* src, float* dst, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!src || !dst))) return HMG_ERR_INVALID_ARG;
+  if (n == 0) return HMG_OK;
+  launch_convert(n, src, HMG_FP64, dst, as_stream(stream));
+  return cudaGetLastError() == cudaSuccess ? HMG_OK : HMG_ERR_CUDA;
+}
+
+hmg_status hmg_convert_fp32_to_fp64(const float* src, double* dst, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!src || !dst))) return HMG_ERR_INVALID_ARG;
+  if (n == 0) return HMG_OK;
+  launch_convert(n, src, HMG_FP32, dst, as_stream(stream));
+  return cudaGetLastError() == cudaSuccess ? HMG_OK : HMG_ERR_CUDA;
 }
 
 hmg_status hmg_sync(hmg_ctx* ctx, void* stream) {

@@ -15,6 +15,7 @@
 // load or store of one layer is a single 256-byte (FP64) or 128-byte (FP32)
 // coalesced access.  The residual/restriction and the operator application
 // are layer parallel: one thread per cell.
+#include "convert.cuh"
 #include "hmg_internal.h"
 #include "reduce.cuh"
 
@@ -36,14 +37,16 @@ struct LD {
   const T* __restrict__ e;
   const T* __restrict__ lo;
   const T* __restrict__ w;
+  const T* __restrict__ mt;   // per column: mu of the twist row
+  int twist;                  // twist row m of the column factorisation
 };
 
 template <typename T> LD<T> view(const Level& L);
 template <> LD<double> view<double>(const Level& L) {
-  return LD<double>{L.nc, L.nz, L.Np, L.nbr, L.gh, L.d, L.e, L.lo, L.w};
+  return LD<double>{L.nc, L.nz, L.Np, L.nbr, L.gh, L.d, L.e, L.lo, L.w, L.mt, L.twist};
 }
 template <> LD<float> view<float>(const Level& L) {
-  return LD<float>{L.nc, L.nz, L.Np, L.nbr, L.gh32, L.d32, L.e32, L.lo32, L.w32};
+  return LD<float>{L.nc, L.nz, L.Np, L.nbr, L.gh32, L.d32, L.e32, L.lo32, L.w32, L.mt32, L.twist};
 }
 
 __device__ __forceinline__ int64_t tile_base(int c, int nz) {
@@ -54,20 +57,50 @@ __device__ __forceinline__ int64_t tile_base(int c, int nz) {
 //
 // One CTA per tile of 32 columns, NW warps, two shared arrays of nz x 32:
 //   A  (all warps, layer parallel)  R = b + sum_k g_k u[nbr_k]   (u~ with PRO)
-//                                   LO = l-multipliers of L D L^T
-//   B  (one warp: lane = column)    forward elimination  y_l = R_l - lo_l y_l-1
-//   B' (all warps)                  y_l *= omega / D_l
-//   C  (one warp)                   back substitution    x_l = y_l - lo_l+1 x_l+1
+//                                   LO = multipliers of the twisted N D N^T
+//   B  (two warps: lane = column)   elimination N y = R: rows 0..m-1 top-down
+//                                   on one warp, rows nz-1..m+1 bottom-up on
+//                                   another (m = twist row of the level)
+//   B' (all warps)                  z_l = (omega / D_l) y_l; row m first
+//                                   completes y_m = R_m - lambda_m y_m-1 - mu_m y_m+1
+//   C  (two warps)                  substitution N^T x = z outwards from row m
 //   D  (all warps)                  u' = (1 - omega) u~ + x
-// Only the two recurrences are sequential, and they read shared memory, so
-// the dependent chain never waits for global memory; everything else is
-// spread over the CTA.  MODE_ZERO is the first pre-smoothing step (u = 0):
+// Only the recurrences are sequential (two chains of about nz / 2 steps on
+// two warps), and they read shared memory, so they never wait for global
+// memory; everything else is spread over the CTA.  MODE_ZERO is the first pre-smoothing step (u = 0):
 // no neighbour sum and no relaxation term.
 enum { MODE_ZERO = 0, MODE_PLAIN = 1, MODE_PRO = 2 };
 
+// count steps of y <- R[l] - LO[l + mshift] y; R[l] = y at l = l0, l0 + step,
+// ...; shared-memory loads are issued four steps ahead of the dependent FMAs.
+template <typename T>
+__device__ __forceinline__ T chain(T* R, const T* LO, int lane, int l0, int step, int mshift, int count, T y) {
+  int k = 0;
+  for (; k + 4 <= count; k += 4) {
+    const int la = l0 + k * step, lb = la + step, lc = lb + step, ld = lc + step;
+    const T r0 = R[la * TW + lane], r1 = R[lb * TW + lane], r2 = R[lc * TW + lane], r3 = R[ld * TW + lane];
+    const T m0 = LO[(la + mshift) * TW + lane], m1 = LO[(lb + mshift) * TW + lane],
+            m2 = LO[(lc + mshift) * TW + lane], m3 = LO[(ld + mshift) * TW + lane];
+    y = fma(-m0, y, r0);
+    R[la * TW + lane] = y;
+    y = fma(-m1, y, r1);
+    R[lb * TW + lane] = y;
+    y = fma(-m2, y, r2);
+    R[lc * TW + lane] = y;
+    y = fma(-m3, y, r3);
+    R[ld * TW + lane] = y;
+  }
+  for (; k < count; ++k) {
+    const int l = l0 + k * step;
+    y = fma(-LO[(l + mshift) * TW + lane], y, R[l * TW + lane]);
+    R[l * TW + lane] = y;
+  }
+  return y;
+}
+
 // DOT = 1: also reduce sum_cells da * u' (the r.z of CG, da = the FP64
 // residual); DOT = 2: and sum_cells u' * dc (the z.q of flexible CG).
-template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT>
+template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT, bool TW2>
 __global__ void __launch_bounds__(NW * 32)
 k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restrict__ uo,
          const TE* __restrict__ ec, float* __restrict__ bcopy, T om1, const double* __restrict__ da,
@@ -75,8 +108,9 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RB = 4;  // rows per warp per batch: their loads are issued together
   const int nz = L.nz;
+  // shared: R[nz][32], two rows for the twist (y_m-1, y_m+1), LO[nz][32]
   T* R = reinterpret_cast<T*>(smem_raw);
-  T* LOs = R + nz * TW;
+  T* LOs = R + (nz + 2) * TW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tile = blockIdx.x;
   const int c = tile * TW + lane;
@@ -106,16 +140,16 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
       bl[i] = lo[i] = a0[i] = a1[i] = a2[i] = 0;
       if (valid && l < nz) {
         const int64_t o = (int64_t)l * TW;
-        bl[i] = (T)b[base + o];
+        bl[i] = cvt<T>(b[base + o]);
         lo[i] = L.lo[base + o];
         if (MODE != MODE_ZERO) {
           a0[i] = u[s0 + o];
           a1[i] = u[s1 + o];
           a2[i] = u[s2 + o];
           if (MODE == MODE_PRO) {
-            a0[i] += (T)ec[q0 + o];
-            a1[i] += (T)ec[q1 + o];
-            a2[i] += (T)ec[q2 + o];
+            a0[i] += cvt<T>(ec[q0 + o]);
+            a1[i] += cvt<T>(ec[q1 + o]);
+            a2[i] += cvt<T>(ec[q2 + o]);
           }
         }
       }
@@ -137,75 +171,124 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
     }
   }
   __syncthreads();
-  const int cw = blockIdx.x % NW;  // spread the chain warps over the sub-partitions
-  // B
-  if (warp == cw) {
-    T y = 0;
-    int l = 0;
-    for (; l + 4 <= nz; l += 4) {
-      T r0 = R[(l + 0) * TW + lane], r1 = R[(l + 1) * TW + lane], r2 = R[(l + 2) * TW + lane],
-        r3 = R[(l + 3) * TW + lane];
-      T m0 = LOs[(l + 0) * TW + lane], m1 = LOs[(l + 1) * TW + lane], m2 = LOs[(l + 2) * TW + lane],
-        m3 = LOs[(l + 3) * TW + lane];
-      y = r0 - m0 * y;
-      R[(l + 0) * TW + lane] = y;
-      y = r1 - m1 * y;
-      R[(l + 1) * TW + lane] = y;
-      y = r2 - m2 * y;
-      R[(l + 2) * TW + lane] = y;
-      y = r3 - m3 * y;
-      R[(l + 3) * TW + lane] = y;
+  if (!TW2) {
+    // one chain warp (plain L D L^T: twist row nz - 1), spread over the sub-partitions
+    const int cw = blockIdx.x % NW;
+    // B
+    if (warp == cw) {
+      T y = 0;
+      int l = 0;
+      for (; l + 4 <= nz; l += 4) {
+        T r0 = R[(l + 0) * TW + lane], r1 = R[(l + 1) * TW + lane], r2 = R[(l + 2) * TW + lane],
+          r3 = R[(l + 3) * TW + lane];
+        T m0 = LOs[(l + 0) * TW + lane], m1 = LOs[(l + 1) * TW + lane], m2 = LOs[(l + 2) * TW + lane],
+          m3 = LOs[(l + 3) * TW + lane];
+        y = r0 - m0 * y;
+        R[(l + 0) * TW + lane] = y;
+        y = r1 - m1 * y;
+        R[(l + 1) * TW + lane] = y;
+        y = r2 - m2 * y;
+        R[(l + 2) * TW + lane] = y;
+        y = r3 - m3 * y;
+        R[(l + 3) * TW + lane] = y;
+      }
+      for (; l < nz; ++l) {
+        y = R[l * TW + lane] - LOs[l * TW + lane] * y;
+        R[l * TW + lane] = y;
+      }
     }
-    for (; l < nz; ++l) {
-      y = R[l * TW + lane] - LOs[l * TW + lane] * y;
-      R[l * TW + lane] = y;
-    }
-  }
-  __syncthreads();
-  // B'
-  for (int l0 = warp; l0 < nz; l0 += RB * NW) {
-    T wv[RB];
+    __syncthreads();
+    // B'
+    for (int l0 = warp; l0 < nz; l0 += RB * NW) {
+      T wv[RB];
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      const int l = l0 + i * NW;
-      wv[i] = (l < nz) ? L.w[base + (int64_t)l * TW] : (T)0;
-    }
+      for (int i = 0; i < RB; ++i) {
+        const int l = l0 + i * NW;
+        wv[i] = (l < nz) ? L.w[base + (int64_t)l * TW] : (T)0;
+      }
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      const int l = l0 + i * NW;
-      if (l < nz) R[l * TW + lane] *= wv[i];
+      for (int i = 0; i < RB; ++i) {
+        const int l = l0 + i * NW;
+        if (l < nz) R[l * TW + lane] *= wv[i];
+      }
     }
+    __syncthreads();
+    // C
+    if (warp == cw) {
+      T x = 0, lnext = 0;
+      int l = nz - 1;
+      for (; l - 3 >= 0; l -= 4) {
+        T z0 = R[l * TW + lane], z1 = R[(l - 1) * TW + lane], z2 = R[(l - 2) * TW + lane],
+          z3 = R[(l - 3) * TW + lane];
+        T m0 = LOs[l * TW + lane], m1 = LOs[(l - 1) * TW + lane], m2 = LOs[(l - 2) * TW + lane],
+          m3 = LOs[(l - 3) * TW + lane];
+        x = z0 - lnext * x;
+        R[l * TW + lane] = x;
+        x = z1 - m0 * x;
+        R[(l - 1) * TW + lane] = x;
+        x = z2 - m1 * x;
+        R[(l - 2) * TW + lane] = x;
+        x = z3 - m2 * x;
+        R[(l - 3) * TW + lane] = x;
+        lnext = m3;
+      }
+      for (; l >= 0; --l) {
+        T mm = LOs[l * TW + lane];
+        x = R[l * TW + lane] - lnext * x;
+        R[l * TW + lane] = x;
+        lnext = mm;
+      }
+    }
+    __syncthreads();
+  } else {
+    // two chain warps on different sub-partitions, spread over the CTAs
+    const int cw0 = blockIdx.x % NW, cw1 = (cw0 + 1) % NW;
+    const int m = L.twist;
+    T* YT = R + nz * TW;   // y_m-1 and y_m+1 kept unscaled for the twist row
+    T* YB = YT + TW;
+    const T mtv = valid ? L.mt[c] : (T)0;
+    // B
+    if (warp == cw0) {
+      T y = chain<T>(R, LOs, lane, 0, +1, 0, m, (T)0);
+      YT[lane] = y;
+    } else if (warp == cw1) {
+      T y = chain<T>(R, LOs, lane, nz - 1, -1, 0, nz - 1 - m, (T)0);
+      YB[lane] = y;
+    }
+    __syncthreads();
+    // B'
+    for (int l0 = warp; l0 < nz; l0 += RB * NW) {
+      T wv[RB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int l = l0 + i * NW;
+        wv[i] = (l < nz) ? L.w[base + (int64_t)l * TW] : (T)0;
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int l = l0 + i * NW;
+        if (l < nz) {
+          T y = R[l * TW + lane];
+          if (l == m) y = fma(-mtv, YB[lane], fma(-LOs[m * TW + lane], YT[lane], y));
+          R[l * TW + lane] = y * wv[i];
+        }
+      }
+    }
+    __syncthreads();
+    // C
+    if (warp == cw0) {
+      chain<T>(R, LOs, lane, m - 1, -1, +1, m, R[m * TW + lane]);
+    } else if (warp == cw1 && m + 1 < nz) {
+      T x = R[(m + 1) * TW + lane] - mtv * R[m * TW + lane];
+      R[(m + 1) * TW + lane] = x;
+      chain<T>(R, LOs, lane, m + 2, +1, -1, nz - 2 - m, x);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // C
-  if (warp == cw) {
-    T x = 0, lnext = 0;
-    int l = nz - 1;
-    for (; l - 3 >= 0; l -= 4) {
-      T z0 = R[l * TW + lane], z1 = R[(l - 1) * TW + lane], z2 = R[(l - 2) * TW + lane],
-        z3 = R[(l - 3) * TW + lane];
-      T m0 = LOs[l * TW + lane], m1 = LOs[(l - 1) * TW + lane], m2 = LOs[(l - 2) * TW + lane],
-        m3 = LOs[(l - 3) * TW + lane];
-      x = z0 - lnext * x;
-      R[l * TW + lane] = x;
-      x = z1 - m0 * x;
-      R[(l - 1) * TW + lane] = x;
-      x = z2 - m1 * x;
-      R[(l - 2) * TW + lane] = x;
-      x = z3 - m2 * x;
-      R[(l - 3) * TW + lane] = x;
-      lnext = m3;
-    }
-    for (; l >= 0; --l) {
-      T m = LOs[l * TW + lane];
-      x = R[l * TW + lane] - lnext * x;
-      R[l * TW + lane] = x;
-      lnext = m;
-    }
-  }
-  __syncthreads();
-  // D
-  double acc0 = 0.0, acc1 = 0.0;
+  // D (one accumulator per row of a batch: no dependent FP64 chain)
+  double acc0[RB], acc1[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) acc0[i] = acc1[i] = 0.0;
   if (valid) {
     for (int l0 = warp; l0 < nz; l0 += RB * NW) {
       T uc[RB];
@@ -216,7 +299,7 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
           uc[i] = 0;
           if (l < nz) {
             uc[i] = u[base + (int64_t)l * TW];
-            if (MODE == MODE_PRO) uc[i] += (T)ec[q + (int64_t)l * TW];
+            if (MODE == MODE_PRO) uc[i] += cvt<T>(ec[q + (int64_t)l * TW]);
           }
         }
       }
@@ -234,15 +317,163 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
         const int l = l0 + i * NW;
         if (l < nz) {
           T xv = R[l * TW + lane];
-          TO out = (MODE == MODE_ZERO) ? (TO)xv : (TO)(om1 * uc[i] + xv);
+          TO out = (MODE == MODE_ZERO) ? cvt<TO>(xv) : cvt<TO>(om1 * uc[i] + xv);
           uo[base + (int64_t)l * TW] = out;
-          if (DOT) acc0 += dav[i] * (double)out;
-          if (DOT == 2) acc1 += (double)out * dcv[i];
+          if (DOT) acc0[i] = fma(dav[i], (double)out, acc0[i]);
+          if (DOT == 2) acc1[i] = fma((double)out, dcv[i], acc1[i]);
         }
       }
     }
   }
-  if (DOT) grid_reduce2(acc0, acc1, red);
+  if (DOT) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      a0 += acc0[i];
+      a1 += acc1[i];
+    }
+    // the tile's shared arrays are free now: reuse them as scratch
+    grid_reduce<(DOT == 2 ? 2 : 1)>(a0, a1, red, reinterpret_cast<double*>(smem_raw));
+  }
+}
+
+// ---------------------------------------------------------------- FP32 staged sweep
+//
+// FP32 cycle (HBM bound): the tile's whole input is copied to shared memory
+// with asynchronous copies issued at once (16-byte copies of the tile's
+// contiguous rows of b, lo, w, u; 4-byte copies of the neighbour columns of
+// u), so a CTA waits for memory once instead of once per phase; the phases
+// then run from shared memory as in k_tsweep.  Padding columns copy zeros
+// (their neighbours are themselves and their coefficients are zero).
+// MODE_ZERO or MODE_PLAIN only (the prolongation is a pass of its own).  Used
+// on small levels: with 4-CTA-per-SM occupancy it loses to k_tsweep on large
+// ones.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int NTH>
+__device__ __forceinline__ void stage_rows(void* dst, const void* src, int bytes) {
+  for (int off = (int)threadIdx.x * 16; off < bytes; off += NTH * 16)
+    cp_async16(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off);
+}
+
+template <typename TB, typename TO, int MODE, int NW, int DOT, bool TW2>
+__global__ void __launch_bounds__(NW * 32)
+k_asweep(LD<float> L, const TB* __restrict__ b, const float* __restrict__ u, TO* __restrict__ uo,
+         float* __restrict__ bcopy, float om1, const double* __restrict__ da, const double* __restrict__ dc,
+         Reduce red) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nz = L.nz;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = blockIdx.x;
+  const int c = tile * TW + lane;
+  const bool valid = c < L.nc;
+  const int cells = nz * TW;
+  const int64_t tb = (int64_t)tile * cells;   // first element of the tile
+  const int64_t base = tb + lane;
+  // shared: Bs (TB), LOs, Ws, [Us, N0 (= R), N1, N2] (float), R for MODE_ZERO, 2 twist rows
+  TB* Bs = reinterpret_cast<TB*>(smem_raw);
+  float* LOs = reinterpret_cast<float*>(Bs + cells);
+  float* Ws = LOs + cells;
+  float* Us = Ws + cells;
+  float* N0 = Us + cells;
+  float* N1 = N0 + cells;
+  float* N2 = N1 + cells;
+  float* R = (MODE == MODE_ZERO) ? Us : N0;
+  float* YT = R + cells;  // MODE_ZERO: the 2 rows after R; otherwise rows after N2
+  if (MODE != MODE_ZERO) YT = N2 + cells;
+  float* YB = YT + TW;
+
+  stage_rows<NW * 32>(Bs, b + tb, cells * (int)sizeof(TB));
+  stage_rows<NW * 32>(LOs, L.lo + tb, cells * 4);
+  stage_rows<NW * 32>(Ws, L.w + tb, cells * 4);
+  typename Vec4<float>::type g{};
+  if (MODE != MODE_ZERO) {
+    stage_rows<NW * 32>(Us, u + tb, cells * 4);
+    const int4 nb = L.nbr[c];
+    g = L.gh[c];
+    const int64_t s0 = tile_base(nb.x, nz), s1 = tile_base(nb.y, nz), s2 = tile_base(nb.z, nz);
+    for (int l = warp; l < nz; l += NW) {
+      const int64_t o = (int64_t)l * TW;
+      cp_async4(N0 + l * TW + lane, u + s0 + o);
+      cp_async4(N1 + l * TW + lane, u + s1 + o);
+      cp_async4(N2 + l * TW + lane, u + s2 + o);
+    }
+  }
+  const float mtv = valid ? L.mt[c] : 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+  // A: R = b + g0 u0 + g1 u1 + g2 u2 (in place over N0, or over Us for MODE_ZERO)
+  for (int l = warp; l < nz; l += NW) {
+    const int i = l * TW + lane;
+    float r = cvt<float>(Bs[i]);
+    if (bcopy && valid) bcopy[base + (int64_t)l * TW] = r;
+    if (MODE != MODE_ZERO) {
+      r = fmaf(g.x, N0[i], r);
+      r = fmaf(g.y, N1[i], r);
+      r = fmaf(g.z, N2[i], r);
+    }
+    R[i] = r;
+  }
+  __syncthreads();
+  const int m = L.twist;
+  if (!TW2) {
+    const int cw = blockIdx.x % NW;
+    if (warp == cw) chain<float>(R, LOs, lane, 0, +1, 0, nz, 0.f);
+  } else {
+    const int cw0 = blockIdx.x % NW, cw1 = (cw0 + 1) % NW;
+    if (warp == cw0) YT[lane] = chain<float>(R, LOs, lane, 0, +1, 0, m, 0.f);
+    else if (warp == cw1) YB[lane] = chain<float>(R, LOs, lane, nz - 1, -1, 0, nz - 1 - m, 0.f);
+  }
+  __syncthreads();
+  // B'
+  for (int l = warp; l < nz; l += NW) {
+    const int i = l * TW + lane;
+    float y = R[i];
+    if (TW2 && l == m) y = fmaf(-mtv, YB[lane], fmaf(-LOs[i], YT[lane], y));
+    R[i] = y * Ws[i];
+  }
+  __syncthreads();
+  // C
+  if (!TW2) {
+    const int cw = blockIdx.x % NW;
+    if (warp == cw) chain<float>(R, LOs, lane, nz - 2, -1, +1, nz - 1, R[(nz - 1) * TW + lane]);
+  } else {
+    const int cw0 = blockIdx.x % NW, cw1 = (cw0 + 1) % NW;
+    if (warp == cw0) {
+      chain<float>(R, LOs, lane, m - 1, -1, +1, m, R[m * TW + lane]);
+    } else if (warp == cw1 && m + 1 < nz) {
+      float x = R[(m + 1) * TW + lane] - mtv * R[m * TW + lane];
+      R[(m + 1) * TW + lane] = x;
+      chain<float>(R, LOs, lane, m + 2, +1, -1, nz - 2 - m, x);
+    }
+  }
+  __syncthreads();
+  // D (two accumulators per dot, alternating rows: no long dependent FP64 chain)
+  double acc0[2] = {0.0, 0.0}, acc1[2] = {0.0, 0.0};
+  if (valid) {
+    int k = 0;
+    for (int l = warp; l < nz; l += NW, ++k) {
+      const int i = l * TW + lane;
+      const float xv = R[i];
+      const TO out = (MODE == MODE_ZERO) ? cvt<TO>(xv) : cvt<TO>(fmaf(om1, Us[i], xv));
+      uo[base + (int64_t)l * TW] = out;
+      if (DOT) acc0[k & 1] = fma(da[base + (int64_t)l * TW], (double)out, acc0[k & 1]);
+      if (DOT == 2) acc1[k & 1] = fma((double)out, dc[base + (int64_t)l * TW], acc1[k & 1]);
+    }
+  }
+  if (DOT)
+    grid_reduce<(DOT == 2 ? 2 : 1)>(acc0[0] + acc0[1], acc1[0] + acc1[1], red, reinterpret_cast<double*>(smem_raw));
 }
 
 // ---------------------------------------------------------------- layer-parallel kernels
@@ -264,7 +495,7 @@ k_tprolong(int nc, int nz, int ntiles, int RG, T* __restrict__ u, const TE* __re
     const int64_t base = (int64_t)tile * TW * nz + lane;
     const int64_t q = tile_base(c >> 2, nz);
 #pragma unroll 4
-    for (int l = row0; l < nz; l += rstep) u[base + (int64_t)l * TW] += (T)ec[q + (int64_t)l * TW];
+    for (int l = row0; l < nz; l += rstep) u[base + (int64_t)l * TW] += cvt<T>(ec[q + (int64_t)l * TW]);
   }
 }
 
@@ -314,7 +545,7 @@ k_tresid_restrict(LD<T> L, int ntiles, int RG, const T* __restrict__ b, const T*
       if (valid) r = stencil_acc<T, -1>(L, u, t, l, b[t], g, s0, s1, s2);
       r += __shfl_xor_sync(0xffffffffu, r, 1);
       r += __shfl_xor_sync(0xffffffffu, r, 2);
-      if ((lane & 3) == 0 && valid) bc[qc + (int64_t)l * TW] = (TC)r;
+      if ((lane & 3) == 0 && valid) bc[qc + (int64_t)l * TW] = cvt<TC>(r);
     }
   }
 }
@@ -326,7 +557,7 @@ k_tapply(LD<T> L, int ntiles, int RG, const T* __restrict__ x, T* __restrict__ y
   const int lane = threadIdx.x & 31;
   const int row0 = (blockIdx.x % RG) * NW + (threadIdx.x >> 5), rstep = RG * NW;
   const int nz = L.nz;
-  double acc = 0.0;
+  double acc[2] = {0.0, 0.0};  // alternate rows: no dependent FP64 chain
   for (int tile = blockIdx.x / RG; tile < ntiles; tile += gridDim.x / RG) {
     const int c = tile * TW + lane;
     const bool valid = c < L.nc;
@@ -340,16 +571,20 @@ k_tapply(LD<T> L, int ntiles, int RG, const T* __restrict__ x, T* __restrict__ y
       s1 = tile_base(nb.y, nz);
       s2 = tile_base(nb.z, nz);
     }
+    int k = 0;
 #pragma unroll 2
-    for (int l = row0; l < nz; l += rstep) {
+    for (int l = row0; l < nz; l += rstep, ++k) {
       const int64_t t = base + (int64_t)l * TW;
       T v = 0;
       if (valid) v = stencil_acc<T, 1>(L, x, t, l, (T)0, g, s0, s1, s2);
       y[t] = v;
-      if (DOT) acc += (double)x[t] * (double)v;
+      if (DOT) acc[k & 1] = fma((double)x[t], (double)v, acc[k & 1]);
     }
   }
-  if (DOT) grid_reduce2(acc, 0.0, red);
+  if (DOT) {
+    HMG_RED_SCRATCH(scratch);
+    grid_reduce<1>(acc[0] + acc[1], 0.0, red, scratch);
+  }
 }
 
 constexpr int NW_PAR = 8;
@@ -358,8 +593,10 @@ constexpr int NW_PAR = 8;
 // one wave), 16 warps on smaller levels (latency bound: each warp loads only
 // a few rows).
 constexpr int NW_SWEEP_BIG = 4;
+// FP32 levels up to this many tiles use the staged sweep (k_asweep): there it
+// beats the register-batched one; on larger levels it does not.
+constexpr int STAGED_MAX_TILES = 160;
 constexpr int NW_SWEEP_SMALL = 16;
-constexpr int SMALL_LEVEL_TILES = 152;
 
 inline int ntiles_of(const Level& L) { return L.ncp / TW; }
 
@@ -385,16 +622,25 @@ void allow_smem(K kern, size_t smem, size_t& configured) {
   }
 }
 
-template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT>
-void tsweep_nw(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
-               const SweepDot* dot, cudaStream_t s) {
-  auto kern = k_tsweep<T, TB, TO, MODE, TE, NW, DOT>;
-  const size_t smem = 2 * (size_t)L.nz * TW * sizeof(T);
+template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT, bool TW2>
+void tsweep_k(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
+              const SweepDot* dot, cudaStream_t s) {
+  auto kern = k_tsweep<T, TB, TO, MODE, TE, NW, DOT, TW2>;
+  size_t smem = (2 * (size_t)L.nz + 2) * TW * sizeof(T);
+  if (DOT && smem < (size_t)DOT * NW * 32 * sizeof(double)) smem = (size_t)DOT * NW * 32 * sizeof(double);
   static size_t configured = 0;
   allow_smem(kern, smem, configured);
   Reduce red = dot ? dot->red : Reduce{};
   kern<<<ntiles_of(L), NW * 32, smem, s>>>(view<T>(L), (const TB*)b, (const T*)u, (TO*)uo, (const TE*)ec, bcopy,
                                           (T)(1.0 - omega), dot ? dot->a : nullptr, dot ? dot->c : nullptr, red);
+}
+
+template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT>
+void tsweep_nw(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
+               const SweepDot* dot, cudaStream_t s) {
+  // small levels (16 warps) use the twisted two-chain solve, large ones the
+  // single chain: capi.cu sets the twist row with the same tile threshold
+  tsweep_k<T, TB, TO, MODE, TE, NW, DOT, (NW == NW_SWEEP_SMALL)>(L, b, u, uo, ec, bcopy, omega, dot, s);
 }
 
 template <typename T, typename TB, typename TO, int MODE, typename TE, int NW>
@@ -403,6 +649,40 @@ void tsweep_dot(const Level& L, const void* b, const void* u, void* uo, const vo
   if (!dot) tsweep_nw<T, TB, TO, MODE, TE, NW, 0>(L, b, u, uo, ec, bcopy, omega, dot, s);
   else if (!dot->c) tsweep_nw<T, TB, TO, MODE, TE, NW, 1>(L, b, u, uo, ec, bcopy, omega, dot, s);
   else tsweep_nw<T, TB, TO, MODE, TE, NW, 2>(L, b, u, uo, ec, bcopy, omega, dot, s);
+}
+
+// FP32 staged sweep: 4 warps on large levels, 8 on small ones (twisted solve)
+template <typename TB, typename TO, int MODE, int NW, int DOT, bool TW2>
+void asweep_k(const Level& L, const void* b, const void* u, void* uo, float* bcopy, double omega,
+              const SweepDot* dot, cudaStream_t s) {
+  auto kern = k_asweep<TB, TO, MODE, NW, DOT, TW2>;
+  const size_t cells = (size_t)L.nz * TW;
+  // b, then lo, w, u (R for MODE_ZERO) and, for MODE_PLAIN, three neighbour arrays, then 2 twist rows
+  size_t smem = cells * sizeof(TB) + (MODE == MODE_ZERO ? 3 : 6) * cells * 4 + 2 * TW * 4;
+  if (DOT && smem < (size_t)DOT * NW * 32 * sizeof(double)) smem = (size_t)DOT * NW * 32 * sizeof(double);
+  static size_t configured = 0;
+  allow_smem(kern, smem, configured);
+  Reduce red = dot ? dot->red : Reduce{};
+  kern<<<ntiles_of(L), NW * 32, smem, s>>>(view<float>(L), (const TB*)b, (const float*)u, (TO*)uo, bcopy,
+                                          (float)(1.0 - omega), dot ? dot->a : nullptr, dot ? dot->c : nullptr,
+                                          red);
+}
+
+template <typename TB, typename TO, int MODE, int DOT>
+void asweep_dot(const Level& L, const void* b, const void* u, void* uo, float* bcopy, double omega,
+                const SweepDot* dot, cudaStream_t s) {
+  if (ntiles_of(L) > SMALL_LEVEL_TILES)
+    asweep_k<TB, TO, MODE, 4, DOT, false>(L, b, u, uo, bcopy, omega, dot, s);
+  else
+    asweep_k<TB, TO, MODE, 8, DOT, true>(L, b, u, uo, bcopy, omega, dot, s);
+}
+
+template <typename TB, typename TO, int MODE>
+void asweep(const Level& L, const void* b, const void* u, void* uo, float* bcopy, double omega, cudaStream_t s,
+            const SweepDot* dot = nullptr) {
+  if (!dot) asweep_dot<TB, TO, MODE, 0>(L, b, u, uo, bcopy, omega, dot, s);
+  else if (!dot->c) asweep_dot<TB, TO, MODE, 1>(L, b, u, uo, bcopy, omega, dot, s);
+  else asweep_dot<TB, TO, MODE, 2>(L, b, u, uo, bcopy, omega, dot, s);
 }
 
 template <typename T, typename TB, typename TO, int MODE, typename TE>
@@ -422,6 +702,8 @@ void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, flo
     tsweep<double, double, double, MODE_ZERO, double>(L, b, nullptr, u, nullptr, nullptr, omega, s);
   else if (b_dt == HMG_FP64)
     tsweep<float, double, float, MODE_ZERO, float>(L, b, nullptr, u, nullptr, bcopy, omega, s);
+  else if (ntiles_of(L) <= STAGED_MAX_TILES)
+    asweep<float, float, MODE_ZERO>(L, b, nullptr, u, nullptr, omega, s);
   else
     tsweep<float, float, float, MODE_ZERO, float>(L, b, nullptr, u, nullptr, nullptr, omega, s);
 }
@@ -435,8 +717,14 @@ void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo
   }
   const bool out64 = uo_dt == HMG_FP64;
   if (!ec) {
-    if (out64) tsweep<float, float, double, MODE_PLAIN, float>(L, b, u, uo, nullptr, nullptr, omega, s, dot);
-    else tsweep<float, float, float, MODE_PLAIN, float>(L, b, u, uo, nullptr, nullptr, omega, s, dot);
+    // small levels: staged sweep (the prolongation, if any, was a pass of its own)
+    if (ntiles_of(L) <= STAGED_MAX_TILES) {
+      if (out64) asweep<float, double, MODE_PLAIN>(L, b, u, uo, nullptr, omega, s, dot);
+      else asweep<float, float, MODE_PLAIN>(L, b, u, uo, nullptr, omega, s, dot);
+    } else {
+      if (out64) tsweep<float, float, double, MODE_PLAIN, float>(L, b, u, uo, nullptr, nullptr, omega, s, dot);
+      else tsweep<float, float, float, MODE_PLAIN, float>(L, b, u, uo, nullptr, nullptr, omega, s, dot);
+    }
   } else if (ec_dt == HMG_FP64) {
     if (out64) tsweep<float, float, double, MODE_PRO, double>(L, b, u, uo, ec, nullptr, omega, s, dot);
     else tsweep<float, float, float, MODE_PRO, double>(L, b, u, uo, ec, nullptr, omega, s, dot);

@@ -8,8 +8,9 @@
 //                        lateral faces and their sum G (layer independent)
 //   d, e  double[Np]     diagonal of H^ and the vertical off-diagonal
 //                        H^[(c,l),(c,l-1)] (e = 0 at l = 0)
-//   lo, w double[Np]     L D L^T factors of H^_z: multipliers l_l (0 at l = 0)
-//                        and omega / D_l
+//   lo, w double[Np]     twisted factorisation N D N^T of H^_z (twist at
+//                        layer `twist`): multipliers and omega / D_l
+//   mt    double[ncp]    the second multiplier of the twist row
 //   *32                  FP32 copies for the mixed-precision cycle
 #pragma once
 
@@ -24,6 +25,8 @@
 namespace hmg {
 
 constexpr int TW = 32;                 // columns per tile
+constexpr int SMALL_LEVEL_TILES = 152;  // levels with at most this many tiles are latency bound
+constexpr int FUSED_PROLONG_MAX_TILES = 160;  // FP64 levels up to this size fuse prolongation into the sweep
 constexpr int RED_MAX_BLOCKS = 16384;  // partial sums of one reduction (>= tiles of the finest level)
 
 struct HostLevel {
@@ -38,6 +41,10 @@ std::vector<HostLevel> build_mesh_hierarchy(int refinement, int nlevels);
 
 struct Level {
   int refinement = 0, nc = 0, ncp = 0, nz = 0;
+  // twist row of the column factorisation: nz / 2 on small levels (two
+  // half-length recurrences, latency bound), nz - 1 elsewhere (one recurrence:
+  // the plain L D L^T, which measured faster on throughput-bound levels)
+  int twist = 0;
   int64_t N = 0, Np = 0;
   std::vector<double> centroid_host;
   std::vector<int32_t> nbr_host;
@@ -49,8 +56,8 @@ struct Level {
   // coefficients
   double4_32a* gh = nullptr;
   float4* gh32 = nullptr;
-  double *d = nullptr, *e = nullptr, *lo = nullptr, *w = nullptr;
-  float *d32 = nullptr, *e32 = nullptr, *lo32 = nullptr, *w32 = nullptr;
+  double *d = nullptr, *e = nullptr, *lo = nullptr, *w = nullptr, *mt = nullptr;
+  float *d32 = nullptr, *e32 = nullptr, *lo32 = nullptr, *w32 = nullptr, *mt32 = nullptr;
   double* theta = nullptr;    // Np
   // cycle work vectors
   // b: right-hand side of this level (restricted residual); ua, ub: smoother
@@ -119,14 +126,16 @@ void launch_to_tiled(const Level& L, int dt, const void* col, void* tiled, cudaS
 void launch_to_column(const Level& L, int dt, const void* tiled, void* col, cudaStream_t s);
 void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,
                 const Reduce& red, cudaStream_t s);  // s0 = a.b, s1 = c.d (c may be null)
+void launch_update_p(const Level& L, double* p, const double* z, const double* sc, cudaStream_t s);
 void launch_update_xr(const Level& L, double* x, double* r, const double* p, const double* q,
                       const Reduce& red, cudaStream_t s);
-void launch_update_p(const Level& L, double* p, const double* z, const double* sc, cudaStream_t s);
 void launch_resid_sq(const Level& L, const double* b, const double* q, const Reduce& red,
                      cudaStream_t s);  // s0 = |b - q|^2
 void launch_check_finite(const Level& L, const double* v, const Reduce& red, cudaStream_t s);
 
 int reduce_grid(int64_t n);
+// FP64 -> FP32 (round to nearest even) or FP32 -> FP64 on the integer pipe
+void launch_convert(int64_t n, const void* src, int src_dt, void* dst, cudaStream_t s);
 
 }  // namespace hmg
 

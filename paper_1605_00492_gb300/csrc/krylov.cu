@@ -2,6 +2,7 @@
 // tiled layout, and the COLUMN <-> TILED layout conversions.  Every kernel
 // that needs a global dot product folds it into the same pass (deterministic
 // grid reduction, reduce.cuh) and forms the Krylov scalar on the device.
+#include "convert.cuh"
 #include "hmg_internal.h"
 #include "reduce.cuh"
 
@@ -33,15 +34,17 @@ __global__ void k_to_column(int nc, int nz, int64_t Np, const T* __restrict__ ti
   if (decode(t, nz, nc, c, l)) col[(int64_t)c * nz + l] = tiled[t];
 }
 
-// s0 = a.b, s1 = c.d (c == nullptr: s1 = 0)
+// s0 = a.b, s1 = c.d (NV = 2)
+template <int NV>
 __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
                       const double* __restrict__ c, const double* __restrict__ d, Reduce red) {
   double s0 = 0.0, s1 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    s0 += a[i] * b[i];
-    if (c) s1 += c[i] * d[i];
+    s0 = fma(a[i], b[i], s0);
+    if (NV == 2) s1 = fma(c[i], d[i], s1);
   }
-  grid_reduce2(s0, s1, red);
+  HMG_RED_SCRATCH(scratch);
+  grid_reduce<NV>(s0, s1, red, scratch);
 }
 
 // x += alpha p; r -= alpha q; s0 = r.r
@@ -55,7 +58,8 @@ __global__ void k_update_xr(int64_t n, double* __restrict__ x, double* __restric
     r[i] = ri;
     s0 += ri * ri;
   }
-  grid_reduce2(s0, 0.0, red);
+  HMG_RED_SCRATCH(scratch);
+  grid_reduce<1>(s0, 0.0, red, scratch);
 }
 
 // p = z + beta p
@@ -74,12 +78,29 @@ __global__ void k_resid_sq(int64_t n, const double* __restrict__ b, const double
     double v = b[i] - q[i];
     s0 += v * v;
   }
-  grid_reduce2(s0, 0.0, red);
+  HMG_RED_SCRATCH(scratch);
+  grid_reduce<1>(s0, 0.0, red, scratch);
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = f64_to_f32(a[i]);
+}
+
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = f32_to_f64(a[i]);
 }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
+
+void launch_convert(int64_t n, const void* src, int src_dt, void* dst, cudaStream_t s) {
+  const int g = reduce_grid(n);
+  if (src_dt == HMG_FP64) k_f64_to_f32<<<g, 256, 0, s>>>(n, (const double*)src, (float*)dst);
+  else k_f32_to_f64<<<g, 256, 0, s>>>(n, (const float*)src, (double*)dst);
+}
 
 int reduce_grid(int64_t n) {
   int64_t b = (n + 255) / 256;
@@ -105,7 +126,8 @@ void launch_to_column(const Level& L, int dt, const void* tiled, void* col, cuda
 
 void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,
                 const Reduce& red, cudaStream_t s) {
-  k_dot<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, a, b, c, d, red);
+  if (c) k_dot<2><<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, a, b, c, d, red);
+  else k_dot<1><<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, a, b, c, d, red);
 }
 
 void launch_update_xr(const Level& L, double* x, double* r, const double* p, const double* q,
@@ -122,7 +144,7 @@ void launch_resid_sq(const Level& L, const double* b, const double* q, const Red
 }
 
 void launch_check_finite(const Level& L, const double* v, const Reduce& red, cudaStream_t s) {
-  k_dot<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, v, v, nullptr, nullptr, red);
+  k_dot<1><<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, v, v, nullptr, nullptr, red);
 }
 
 }  // namespace hmg

@@ -11,30 +11,28 @@
 
 namespace hmg {
 
-__device__ __forceinline__ void warp_sum2(double& a, double& b) {
+// Block-wide sum of NV (1 or 2) values per thread with few FP64
+// instructions (FP64 adds are expensive on GB300): every thread writes its
+// values to shared memory, then warp 0 adds blockDim / 32 values per lane and
+// finishes with five shuffle steps.  The order is fixed, so the result is
+// deterministic.  Valid in thread 0; blockDim.x a multiple of 32.  `sm` is
+// shared scratch of NV * blockDim.x doubles (free for the block's use).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[2], double* sm) {
+  __syncthreads();  // protect sm from a previous use in the same kernel
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, off);
-    b += __shfl_xor_sync(0xffffffffu, b, off);
-  }
-}
-
-// Block-wide sum; the result is valid in thread 0.  blockDim.x <= 1024.
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[32], sb[32];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  warp_sum2(a, b);
-  __syncthreads();  // protect sa/sb from a previous use in the same kernel
-  if (lane == 0) {
-    sa[warp] = a;
-    sb[warp] = b;
-  }
+  for (int k = 0; k < NV; ++k) sm[k * blockDim.x + threadIdx.x] = v[k];
   __syncthreads();
-  if (warp == 0) {
-    int nw = (blockDim.x + 31) >> 5;
-    a = lane < nw ? sa[lane] : 0.0;
-    b = lane < nw ? sb[lane] : 0.0;
-    warp_sum2(a, b);
+  if (threadIdx.x < 32) {
+    const int per = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = sm[k * blockDim.x + threadIdx.x];
+      for (int j = 1; j < per; ++j) a += sm[k * blockDim.x + threadIdx.x + 32 * j];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+      v[k] = a;
+    }
   }
 }
 
@@ -82,13 +80,16 @@ __device__ __forceinline__ void reduce_epilogue(const Reduce& red, double s0, do
 }
 
 // Called by every thread of every block of the grid exactly once, after the
-// thread has accumulated its (a, b).  gridDim.x <= RED_MAX_BLOCKS.
-__device__ __forceinline__ void grid_reduce2(double a, double b, const Reduce& red) {
+// thread has accumulated its values (v[1] is ignored when NV = 1).
+// gridDim.x <= RED_MAX_BLOCKS; sm: shared scratch of NV * blockDim.x doubles.
+template <int NV>
+__device__ __forceinline__ void grid_reduce(double v0, double v1, const Reduce& red, double* sm) {
   __shared__ bool is_last;
-  block_sum2(a, b);
+  double v[2] = {v0, NV == 2 ? v1 : 0.0};
+  block_sum<NV>(v, sm);
   if (threadIdx.x == 0) {
-    red.partials[2 * blockIdx.x] = a;
-    red.partials[2 * blockIdx.x + 1] = b;
+    red.partials[2 * blockIdx.x] = v[0];
+    red.partials[2 * blockIdx.x + 1] = NV == 2 ? v[1] : 0.0;
     __threadfence();
     unsigned ticket = atomicAdd(red.counter, 1u);
     is_last = (ticket == gridDim.x - 1);
@@ -96,17 +97,21 @@ __device__ __forceinline__ void grid_reduce2(double a, double b, const Reduce& r
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  double x = 0.0, y = 0.0;
+  double w[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    x += __ldcg(red.partials + 2 * i);
-    y += __ldcg(red.partials + 2 * i + 1);
+    w[0] += __ldcg(red.partials + 2 * i);
+    if (NV == 2) w[1] += __ldcg(red.partials + 2 * i + 1);
   }
-  block_sum2(x, y);
+  block_sum<NV>(w, sm);
   if (threadIdx.x == 0) {
-    reduce_epilogue(red, x, y);
+    reduce_epilogue(red, w[0], NV == 2 ? w[1] : 0.0);
     *red.counter = 0u;
     __threadfence();
   }
 }
+
+// Static shared scratch for kernels of at most 256 threads without dynamic
+// shared memory.
+#define HMG_RED_SCRATCH(name) __shared__ double name[2 * 256]
 
 }  // namespace hmg

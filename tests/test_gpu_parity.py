@@ -279,3 +279,25 @@ def test_tracing_counts_kernels_inside_graphs():
     n0 = c.h.launch_count()
     c.h.solve(b)
     assert c.h.launch_count() > n0
+
+
+def test_integer_pipe_conversions_match_hardware_bitwise():
+    """FP64 -> FP32 (roundTiesToEven) and FP32 -> FP64 of the mixed cycle,
+    against the hardware conversions, bit for bit: random values over the
+    whole exponent range, exact ties, carries into the exponent, the float
+    range limits, subnormals, zeros, infinities and NaN."""
+    rng = np.random.default_rng(5)
+    vals = [rng.standard_normal(200000) * np.exp(rng.uniform(-180, 180, 200000))]
+    f = rng.standard_normal(5000).astype(np.float32).astype(np.float64)
+    ulp = np.abs(f) * 2.0 ** -24
+    vals += [f, f + ulp, f - ulp, f + 0.5 * ulp, f + 1.5 * ulp, f + 0.49 * ulp]      # ties and near-ties
+    big = float(np.finfo(np.float32).max)
+    vals.append(np.array([0.0, -0.0, 1.0, -1.0, big, -big, big * (1 + 2.0 ** -25), big * (1 + 2.0 ** -23),
+                          2.0 ** -126, 2.0 ** -127, 2.0 ** -149, 2.0 ** -150, 1e-45, 1e-300, 1e300,
+                          np.inf, -np.inf, np.nan, 1 - 2.0 ** -25, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24]))
+    x = torch.tensor(np.concatenate(vals), dtype=torch.float64, device=DEV)
+    mine = hmg.convert(x, torch.float32)
+    hw = x.to(torch.float32)
+    assert torch.equal(mine.view(torch.int32), hw.view(torch.int32))
+    back = hmg.convert(hw, torch.float64)
+    assert torch.equal(back.view(torch.int64), hw.to(torch.float64).view(torch.int64))
