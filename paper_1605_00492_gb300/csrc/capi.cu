@@ -269,9 +269,15 @@ SweepDot beta_dot(const hmg_ctx* c, bool flexible) {
   return d;
 }
 
+// Whether the beta dots ride on the V-cycle's last sweep: the FP64 cycle with
+// a last sweep (not a lone sweep0); the FP32 register sweeps take no dots.
+bool fused_beta(const hmg_ctx* c, const CycleCfg& cfg) {
+  return !cfg.mixed && (c->lv.size() > 1 || cfg.n_coarse > 1);
+}
+
 void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
   Level& L = c->lv[0];
-  if (c->lv.size() > 1 || cfg.n_coarse > 1) {
+  if (fused_beta(c, cfg)) {
     SweepDot d = beta_dot(c, flexible);
     cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s, &d);
   } else {
@@ -377,7 +383,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     st = HMG_OK;
   } else {
     // first iteration: p = z = V r
-    if (c->lv.size() > 1 || cfg.n_coarse > 1) {
+    if (fused_beta(c, cfg)) {
       SweepDot d;
       d.a = c->kr;
       d.red = red_with(c, EPI_INIT_RZ);

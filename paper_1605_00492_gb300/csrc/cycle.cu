@@ -476,6 +476,76 @@ k_asweep(LD<float> L, const TB* __restrict__ b, const float* __restrict__ u, TO*
     grid_reduce<(DOT == 2 ? 2 : 1)>(acc0[0] + acc0[1], acc1[0] + acc1[1], red, reinterpret_cast<double*>(smem_raw));
 }
 
+// ---------------------------------------------------------------- FP32 register sweep
+//
+// Large FP32 levels with a fixed layer count NZ (16, 32 or 64): one warp per
+// tile, one lane per column, the whole column in registers.  The forward
+// loop is fully unrolled, so the loads of all layers are free to run ahead of
+// the (short, FP32) elimination chain; no shared memory and no barrier, so
+// many tiles are in flight per SM.  Plain L D L^T (twist row nz - 1).
+template <int NZ, typename TB, typename TO, int MODE, typename TE>
+__global__ void __launch_bounds__(128)
+k_rsweep(LD<float> L, int ntiles, const TB* __restrict__ b, const float* __restrict__ u, TO* __restrict__ uo,
+         const TE* __restrict__ ec, float* __restrict__ bcopy, float om1) {
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (tile >= ntiles) return;
+  const int c = tile * TW + lane;
+  if (c >= L.nc) return;  // padding columns stay zero
+  const int64_t base = (int64_t)tile * TW * NZ + lane;
+  typename Vec4<float>::type g{};
+  int64_t s0 = 0, s1 = 0, s2 = 0, q = 0, q0 = 0, q1 = 0, q2 = 0;
+  if (MODE != MODE_ZERO) {
+    const int4 nb = L.nbr[c];
+    g = L.gh[c];
+    s0 = tile_base(nb.x, NZ);
+    s1 = tile_base(nb.y, NZ);
+    s2 = tile_base(nb.z, NZ);
+    if (MODE == MODE_PRO) {
+      q = tile_base(c >> 2, NZ);
+      q0 = tile_base(nb.x >> 2, NZ);
+      q1 = tile_base(nb.y >> 2, NZ);
+      q2 = tile_base(nb.z >> 2, NZ);
+    }
+  }
+  float y[NZ], lo[NZ];
+  float yp = 0.f;
+#pragma unroll
+  for (int l = 0; l < NZ; ++l) {
+    const int64_t o = (int64_t)l * TW;
+    float r = cvt<float>(b[base + o]);
+    if (bcopy) bcopy[base + o] = r;
+    if (MODE != MODE_ZERO) {
+      float a0 = u[s0 + o], a1 = u[s1 + o], a2 = u[s2 + o];
+      if (MODE == MODE_PRO) {
+        a0 += cvt<float>(ec[q0 + o]);
+        a1 += cvt<float>(ec[q1 + o]);
+        a2 += cvt<float>(ec[q2 + o]);
+      }
+      r = fmaf(g.x, a0, r);
+      r = fmaf(g.y, a1, r);
+      r = fmaf(g.z, a2, r);
+    }
+    lo[l] = L.lo[base + o];
+    yp = fmaf(-lo[l], yp, r);
+    y[l] = yp;
+  }
+  float x = 0.f;
+#pragma unroll
+  for (int l = NZ - 1; l >= 0; --l) {
+    const int64_t o = (int64_t)l * TW;
+    const float lnext = (l + 1 < NZ) ? lo[l + 1] : 0.f;
+    x = fmaf(-lnext, x, L.w[base + o] * y[l]);
+    float out = x;
+    if (MODE != MODE_ZERO) {
+      float uc = u[base + o];
+      if (MODE == MODE_PRO) uc += cvt<float>(ec[q + o]);
+      out = fmaf(om1, uc, x);
+    }
+    uo[base + o] = cvt<TO>(out);
+  }
+}
+
 // ---------------------------------------------------------------- layer-parallel kernels
 // A CTA of NW warps handles row group rg of tiles blockIdx.x / RG (grid-stride
 // over tiles); warp w of row group rg handles the layers rg * NW + w + k * RG * NW;
@@ -685,6 +755,33 @@ void asweep(const Level& L, const void* b, const void* u, void* uo, float* bcopy
   else asweep_dot<TB, TO, MODE, 2>(L, b, u, uo, bcopy, omega, dot, s);
 }
 
+// Large FP32 levels: the register sweep when the layer count has an
+// instantiation (16, 32, 64); returns false otherwise.
+template <typename TB, typename TO, int MODE, typename TE>
+bool rsweep(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
+            cudaStream_t s) {
+  const int nt = ntiles_of(L);
+  const unsigned grid = (unsigned)((nt + 3) / 4);
+  const LD<float> v = view<float>(L);
+  const float om1 = (float)(1.0 - omega);
+  switch (L.nz) {
+    case 16:
+      k_rsweep<16, TB, TO, MODE, TE><<<grid, 128, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
+                                                         (const TE*)ec, bcopy, om1);
+      return true;
+    case 32:
+      k_rsweep<32, TB, TO, MODE, TE><<<grid, 128, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
+                                                         (const TE*)ec, bcopy, om1);
+      return true;
+    case 64:
+      k_rsweep<64, TB, TO, MODE, TE><<<grid, 128, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
+                                                         (const TE*)ec, bcopy, om1);
+      return true;
+    default:
+      return false;
+  }
+}
+
 template <typename T, typename TB, typename TO, int MODE, typename TE>
 void tsweep(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
             cudaStream_t s, const SweepDot* dot = nullptr) {
@@ -700,6 +797,12 @@ void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, flo
                    cudaStream_t s) {
   if (dt == HMG_FP64)
     tsweep<double, double, double, MODE_ZERO, double>(L, b, nullptr, u, nullptr, nullptr, omega, s);
+  else if (ntiles_of(L) > STAGED_MAX_TILES && b_dt == HMG_FP64 &&
+           rsweep<double, float, MODE_ZERO, float>(L, b, nullptr, u, nullptr, bcopy, omega, s))
+    return;
+  else if (ntiles_of(L) > STAGED_MAX_TILES && b_dt != HMG_FP64 &&
+           rsweep<float, float, MODE_ZERO, float>(L, b, nullptr, u, nullptr, nullptr, omega, s))
+    return;
   else if (b_dt == HMG_FP64)
     tsweep<float, double, float, MODE_ZERO, float>(L, b, nullptr, u, nullptr, bcopy, omega, s);
   else if (ntiles_of(L) <= STAGED_MAX_TILES)
@@ -716,6 +819,20 @@ void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo
     return;
   }
   const bool out64 = uo_dt == HMG_FP64;
+  if (ntiles_of(L) > STAGED_MAX_TILES && !dot) {  // large levels: register sweep when it applies
+    bool done = false;
+    if (!ec) {
+      done = out64 ? rsweep<float, double, MODE_PLAIN, float>(L, b, u, uo, nullptr, nullptr, omega, s)
+                   : rsweep<float, float, MODE_PLAIN, float>(L, b, u, uo, nullptr, nullptr, omega, s);
+    } else if (ec_dt == HMG_FP64) {
+      done = out64 ? rsweep<float, double, MODE_PRO, double>(L, b, u, uo, ec, nullptr, omega, s)
+                   : rsweep<float, float, MODE_PRO, double>(L, b, u, uo, ec, nullptr, omega, s);
+    } else {
+      done = out64 ? rsweep<float, double, MODE_PRO, float>(L, b, u, uo, ec, nullptr, omega, s)
+                   : rsweep<float, float, MODE_PRO, float>(L, b, u, uo, ec, nullptr, omega, s);
+    }
+    if (done) return;
+  }
   if (!ec) {
     // small levels: staged sweep (the prolongation, if any, was a pass of its own)
     if (ntiles_of(L) <= STAGED_MAX_TILES) {
