@@ -55,7 +55,10 @@ typedef enum {
 typedef enum { HMG_FP64 = 0, HMG_FP32 = 1 } hmg_dtype;
 typedef enum { HMG_LAYOUT_COLUMN = 0, HMG_LAYOUT_TILED = 1 } hmg_layout;
 typedef enum { HMG_PRECISION_FP64 = 0, HMG_PRECISION_MIXED = 1 } hmg_precision;
-typedef enum { HMG_KRYLOV_CG = 0, HMG_KRYLOV_FCG = 1 } hmg_krylov;
+typedef enum { HMG_KRYLOV_CG = 0, HMG_KRYLOV_FCG = 1, HMG_KRYLOV_GMRES = 2 } hmg_krylov;
+
+/* Largest GMRES restart length (basis vectors kept per cycle). */
+#define HMG_GMRES_MAX_RESTART 32
 
 /* Shell and hierarchy (Sec. 3.1, Sec. 4.1, Table "Grid setup"). */
 typedef struct {
@@ -79,12 +82,14 @@ typedef struct {
 
 typedef struct {
   int precision;        /* hmg_precision */
-  int krylov;           /* hmg_krylov; MIXED always runs flexible CG */
+  int krylov;           /* hmg_krylov; MIXED runs flexible CG for CG and FCG */
   double rtol;          /* stop when ||r_k||_2 / ||b||_2 < rtol (1e-8) */
-  int max_iter;         /* >= 1 */
+  int max_iter;         /* >= 1; for GMRES, Arnoldi steps over all restart cycles */
   int nu_pre;           /* pre-smoothing sweeps per level, >= 1 (2) */
   int nu_post;          /* post-smoothing sweeps per level, >= 1 (2) */
   int n_coarse;         /* smoother iterations on the coarsest level, >= 1 (2) */
+  int restart;          /* GMRES restart length m, 1..HMG_GMRES_MAX_RESTART (30);
+                           ignored by CG and FCG */
 } hmg_solve_params;
 
 typedef struct {
@@ -152,12 +157,18 @@ hmg_status hmg_apply(hmg_ctx* ctx, int level, int dtype, int layout,
 hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r,
                       void* z, int nu_pre, int nu_post, int n_coarse, void* stream);
 
-/* Solve H^ x = b on the finest level with CG (or flexible CG) preconditioned
- * by one V-cycle per iteration, x_0 = 0 (Sec. 5; CG because H^ is symmetric
- * positive definite).  b, x: FP64 device vectors, COLUMN layout, ncells.
- * Blocks until the solve has finished.  Returns NOT_CONVERGED (info filled in)
- * when max_iter is reached, NONFINITE for a non-finite b or residual,
- * BREAKDOWN when p.q <= 0 or r.z <= 0. */
+/* Solve H^ x = b on the finest level with a Krylov method preconditioned by
+ * one V-cycle per iteration, x_0 = 0 (Sec. 5): CG (H^ is symmetric positive
+ * definite), flexible CG, or restarted GMRES(m), the paper's outer method, in
+ * its flexible right-preconditioned form (Saad, Algorithm 9.6: Arnoldi with
+ * classical Gram-Schmidt applied twice, Givens rotations, the iterate formed
+ * at the end of each restart cycle, stopping on the least-squares residual
+ * ||r_k|| / ||b|| < rtol).  GMRES keeps 2m + 1 finest-level FP64 vectors,
+ * allocated by the first GMRES solve that needs them.  b, x: FP64 device
+ * vectors, COLUMN layout, ncells.  Blocks until the solve has finished.
+ * Returns NOT_CONVERGED (info filled in) when max_iter is reached, NONFINITE
+ * for a non-finite b or residual, BREAKDOWN when p.q <= 0 or r.z <= 0 (CG)
+ * or a zero rotation (GMRES), OOM when the GMRES basis cannot be allocated. */
 hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x,
                      const hmg_solve_params* params, hmg_solve_info* info, void* stream);
 
@@ -227,7 +238,8 @@ typedef enum {
   HMG_K_RESID_SQ = 9,        /* |b - H^ x|^2 */
   HMG_K_ASSEMBLY = 10,
   HMG_K_THETA_GRAD = 11,
-  HMG_K_COUNT = 12
+  HMG_K_ORTHO = 12,          /* GMRES: Gram-Schmidt passes, basis start, iterate update */
+  HMG_K_COUNT = 13
 } hmg_kernel_id;
 
 typedef struct {

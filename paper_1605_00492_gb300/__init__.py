@@ -26,7 +26,7 @@ STATUS = {
 FP64, FP32 = 0, 1
 LAYOUT = {"column": 0, "tiled": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
-KRYLOV = {"cg": 0, "fcg": 1}
+KRYLOV = {"cg": 0, "fcg": 1, "gmres": 2}
 
 
 class HMGError(RuntimeError):
@@ -49,7 +49,7 @@ class OpParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
-                ("n_coarse", ctypes.c_int)]
+                ("n_coarse", ctypes.c_int), ("restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -66,7 +66,7 @@ class KernelStat(ctypes.Structure):
 
 
 KERNELS = ["sweep0", "sweep", "prolong", "resid_restrict", "apply", "dot", "update_xr", "update_p", "layout",
-           "resid_sq", "assembly", "theta_grad"]
+           "resid_sq", "assembly", "theta_grad", "ortho"]
 
 
 class LevelInfo(ctypes.Structure):
@@ -222,11 +222,12 @@ class Hierarchy:
         return z
 
     def solve_params(self, precision="fp64", krylov="cg", rtol=1e-8, max_iter=500, nu_pre=2, nu_post=2,
-                     n_coarse=2):
-        return SolveParams(PRECISION[precision], KRYLOV[krylov], rtol, max_iter, nu_pre, nu_post, n_coarse)
+                     n_coarse=2, restart=30):
+        return SolveParams(PRECISION[precision], KRYLOV[krylov], rtol, max_iter, nu_pre, nu_post, n_coarse,
+                           restart)
 
     def solve(self, b, out=None, stream=None, raise_on_failure=True, **kw):
-        """x = H^^-1 b by preconditioned CG; returns (x, info dict)."""
+        """x = H^^-1 b by V-cycle-preconditioned CG, flexible CG or GMRES(restart); returns (x, info dict)."""
         assert b.is_cuda and b.dtype == torch.float64 and b.numel() == self.ncells
         b = b.contiguous()
         x = out if out is not None else torch.empty_like(b)

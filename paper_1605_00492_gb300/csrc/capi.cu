@@ -1,6 +1,7 @@
 // C ABI of the library (include/hmg.h): context life cycle, assembly driver,
 // V-cycle driver (Algorithm 1, recursive correction scheme) and the
-// preconditioned CG / flexible CG loop (Sec. 5).
+// preconditioned CG / flexible CG / restarted flexible GMRES loops (Sec. 5).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -44,6 +45,13 @@ T* dalloc(hmg_ctx* c, size_t count) {
   return static_cast<T*>(p);
 }
 
+void dfree(hmg_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+  if (it != c->allocations.end()) c->allocations.erase(it);
+  cudaFree(p);
+}
+
 void destroy_graph_prof(std::vector<GraphProf>& v) {
   for (auto& gp : v) {
     if (gp.a) cudaEventDestroy(gp.a);
@@ -57,6 +65,8 @@ void release(hmg_ctx* c) {
   c->allocations.clear();
   if (c->host_sc) cudaFreeHost(c->host_sc);
   c->host_sc = nullptr;
+  if (c->gm_host) cudaFreeHost(c->gm_host);
+  c->gm_host = nullptr;
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   c->ev0 = c->ev1 = nullptr;
@@ -270,7 +280,9 @@ SweepDot beta_dot(const hmg_ctx* c, bool flexible) {
 }
 
 // Whether the beta dots ride on the V-cycle's last sweep: the FP64 cycle with
-// a last sweep (not a lone sweep0); the FP32 register sweeps take no dots.
+// a last sweep (not a lone sweep0); the FP32 register sweeps take no dots
+// (holding their outputs for the dots costs the registers that let the
+// column recurrence run ahead of its loads).
 bool fused_beta(const hmg_ctx* c, const CycleCfg& cfg) {
   return !cfg.mixed && (c->lv.size() > 1 || cfg.n_coarse > 1);
 }
@@ -294,15 +306,19 @@ void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t
           "scalar read");
 }
 
-int graph_key(const CycleCfg& cfg, bool flexible) {
-  return ((((cfg.mixed ? 1 : 0) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 + cfg.nu_post) * 65 + cfg.n_coarse;
+// Graph keys: the cycle configuration, the Krylov method and, for GMRES, the
+// Arnoldi step j within a restart cycle (its vectors are baked in).
+int64_t graph_key(const CycleCfg& cfg, bool flexible, int gmres_step = -1) {
+  const int64_t base =
+      ((((cfg.mixed ? 1 : 0) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 + cfg.nu_post) * 65 + cfg.n_coarse;
+  return base * (GMRES_MAX_RESTART + 1) + (gmres_step + 1);
 }
 
 // Replay (capturing it the first time) the iteration body as a CUDA graph.
 // With tracing on, the graph carries event nodes around the traced kernels;
 // harvest_body() reads them after the replay has completed.
-hmg_ctx::BodyGraph* run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
-  const int key = graph_key(cfg, flexible);
+template <typename Body>
+hmg_ctx::BodyGraph* run_graph(hmg_ctx* c, int64_t key, Body&& body, cudaStream_t s) {
   const unsigned long long trace =
       c->prof_on ? (((unsigned long long)c->prof_kmask << 32) | c->prof_lmask) | (1ull << 63) : 0ull;
   hmg_ctx::BodyGraph* g = nullptr;
@@ -316,7 +332,7 @@ hmg_ctx::BodyGraph* run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cud
     cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
     c->capturing = true;
     try {
-      iteration_body(c, cfg, flexible, cs);
+      body(cs);
     } catch (...) {
       c->capturing = false;
       cudaStreamEndCapture(cs, &graph);
@@ -344,6 +360,10 @@ hmg_ctx::BodyGraph* run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cud
   return g;
 }
 
+hmg_ctx::BodyGraph* run_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
+  return run_graph(c, graph_key(cfg, flexible), [&](cudaStream_t cs) { iteration_body(c, cfg, flexible, cs); }, s);
+}
+
 // After the replay of g has completed: add its traced kernels to the records.
 void harvest_body(hmg_ctx* c, const hmg_ctx::BodyGraph* g) {
   if (!c->prof_on || !g) return;
@@ -354,7 +374,11 @@ void harvest_body(hmg_ctx* c, const hmg_ctx::BodyGraph* g) {
   }
 }
 
+hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s);
+
+// The solve on the tiled vectors kb (right-hand side) and kx (solution).
 hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  if (p.krylov == HMG_KRYLOV_GMRES) return solve_gmres(c, p, info, s);
   Level& L = c->lv[0];
   CycleCfg cfg;
   cfg.nu_pre = p.nu_pre;
@@ -435,10 +459,199 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   return st;
 }
 
+// ------------------------------------------------------------ GMRES
+
+// Offsets in gm_small (device) and gm_host (page-locked): the step results
+// h, h2 (with |w|^2 after them) and hn are read back together; y is staged.
+constexpr int GM_H = 0, GM_H2 = GMRES_MAX_RESTART, GM_HN = 2 * GMRES_MAX_RESTART + 1, GM_READ = GM_HN + 1,
+              GM_Y = 3 * GMRES_MAX_RESTART, GM_SMALL = 4 * GMRES_MAX_RESTART;
+
+// Basis storage for restart length m (kept across solves; a longer restart
+// reallocates it and drops the graphs that hold the old vectors).
+void ensure_gmres(hmg_ctx* c, int m) {
+  Level& L = c->lv[0];
+  if (!c->gm_host) {
+    double* small = dalloc<double>(c, GM_SMALL);
+    c->gm.h = small + GM_H;
+    c->gm.h2 = small + GM_H2;
+    c->gm.hn = small + GM_HN;
+    c->gm_y = small + GM_Y;
+    c->gm.part = dalloc<double>(c, (size_t)(GMRES_MAX_RESTART + 1) * GS_MAX_BLOCKS);
+    c->gm.counter = dalloc<unsigned int>(c, 1);
+    cuda_ok(cudaMallocHost(&c->gm_host, GM_SMALL * sizeof(double)), "cudaMallocHost");
+  }
+  if (m <= c->gm_m) return;
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    destroy_graph_prof(g.prof);
+  }
+  c->graphs.clear();
+  dfree(c, c->gm_V);
+  dfree(c, c->gm_Z);
+  c->gm_V = c->gm_Z = nullptr;
+  c->gm_m = 0;
+  c->gm_V = dalloc<double>(c, (size_t)(m + 1) * L.Np);
+  c->gm_Z = dalloc<double>(c, (size_t)m * L.Np);
+  c->gm_m = m;
+}
+
+// Arnoldi step j: z_j = V v_j, w = H^ z_j into v_(j+1), two Gram-Schmidt
+// passes against v_0..v_j and the normalisation, results copied to the host.
+void gmres_step(hmg_ctx* c, const CycleCfg& cfg, int j, cudaStream_t s) {
+  Level& L = c->lv[0];
+  const int64_t ld = L.Np;
+  double* vj = c->gm_V + j * ld;
+  double* zj = c->gm_Z + j * ld;
+  double* w = c->gm_V + (j + 1) * ld;
+  cycle(c, cfg, 0, vj, HMG_FP64, zj, HMG_FP64, s);
+  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, zj, w, nullptr, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_dots(L, c->gm_V, ld, j + 1, w, c->gm, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_update(L, c->gm_V, ld, j + 1, w, c->gm, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_final(L, c->gm_V, ld, j + 1, w, c->gm, s));
+  cuda_ok(cudaMemcpyAsync(c->gm_host, c->gm.h, GM_READ * sizeof(double), cudaMemcpyDeviceToHost, s),
+          "GMRES read");
+}
+
+hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  Level& L = c->lv[0];
+  CycleCfg cfg;
+  cfg.nu_pre = p.nu_pre;
+  cfg.nu_post = p.nu_post;
+  cfg.n_coarse = p.n_coarse;
+  cfg.mixed = p.precision == HMG_PRECISION_MIXED;
+  cfg.omega = c->ph.omega;
+  const int m = p.restart;
+  ensure_gmres(c, m);
+  const int64_t ld = L.Np;
+  hmg_solve_info inf{};
+
+  cuda_ok(cudaEventRecord(c->ev0, s), "event");
+  cuda_ok(cudaMemsetAsync(c->red.sc, 0, S_COUNT * sizeof(double), s), "memset");
+  cuda_ok(cudaMemsetAsync(c->kx, 0, (size_t)ld * sizeof(double), s), "memset");
+  LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, c->kb, c->kb, nullptr, nullptr, red_with(c, EPI_STORE0, S_BB), s));
+  read_scalars(c, s);
+  const double bb = c->host_sc[S_BB];
+  if (((int)c->host_sc[S_FLAG] & F_NONFINITE) || !std::isfinite(bb)) {
+    if (info) *info = inf;
+    throw Fail{HMG_ERR_NONFINITE, "right-hand side is not finite"};
+  }
+  hmg_status st = HMG_ERR_NOT_CONVERGED;
+  if (bb == 0.0) {
+    inf.converged = 1;
+    st = HMG_OK;
+  } else {
+    const double r0 = std::sqrt(bb);
+    LAUNCH(c, HMG_K_ORTHO, 0, s, launch_normalise(L, c->kb, c->gm_V, c->red.sc + S_BB, s));
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    double beta = r0;
+    int k = 0;
+    bool stop = false;
+    while (!stop) {
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        hmg_ctx::BodyGraph* gr =
+            run_graph(c, graph_key(cfg, true, j), [&](cudaStream_t cs) { gmres_step(c, cfg, j, cs); }, s);
+        cuda_ok(cudaStreamSynchronize(s), "solve");
+        harvest_body(c, gr);
+        const double* hh = c->gm_host;
+        bool finite = std::isfinite(hh[GM_HN]) && std::isfinite(hh[GM_H2 + j + 1]);
+        for (int i = 0; i <= j; ++i) {
+          Hij(i, j) = hh[GM_H + i] + hh[GM_H2 + i];
+          finite = finite && std::isfinite(Hij(i, j));
+        }
+        Hij(j + 1, j) = hh[GM_HN];
+        if (!finite) {
+          st = HMG_ERR_NONFINITE;
+          stop = true;
+          break;
+        }
+        for (int i = 0; i < j; ++i) {  // earlier rotations on column j
+          const double a = Hij(i, j), b = Hij(i + 1, j);
+          Hij(i, j) = cs[i] * a + sn[i] * b;
+          Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+        }
+        const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+        if (!(den > 0.0)) {
+          st = HMG_ERR_BREAKDOWN;
+          stop = true;
+          break;
+        }
+        cs[j] = Hij(j, j) / den;
+        sn[j] = Hij(j + 1, j) / den;
+        Hij(j, j) = den;
+        Hij(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++k;
+        jend = j + 1;
+        inf.iterations = k;
+        inf.rel_residual = std::fabs(g[j + 1]) / r0;
+        if (inf.rel_residual < p.rtol) {
+          inf.converged = 1;
+          st = HMG_OK;
+          stop = true;
+          break;
+        }
+        if (k >= p.max_iter) {
+          stop = true;
+          break;
+        }
+      }
+      if (jend > 0) {  // y = R^-1 g; x += Z y
+        for (int i = jend - 1; i >= 0; --i) {
+          double t = g[i];
+          for (int l = i + 1; l < jend; ++l) t -= Hij(i, l) * y[l];
+          y[i] = t / Hij(i, i);
+        }
+        std::copy(y.begin(), y.begin() + jend, c->gm_host + GM_Y);
+        cuda_ok(cudaMemcpyAsync(c->gm_y, c->gm_host + GM_Y, jend * sizeof(double), cudaMemcpyHostToDevice, s),
+                "GMRES y");
+        LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gmres_x(L, c->kx, c->gm_Z, ld, jend, c->gm_y, s));
+      }
+      if (stop) break;
+      // restart from the residual of the new iterate: v_0 = (b - H^ x) / beta
+      LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s));
+      LAUNCH(c, HMG_K_ORTHO, 0, s, launch_sub_norm(L, c->kb, c->kq, c->gm_V, red_with(c, EPI_STORE0, S_RR), s));
+      read_scalars(c, s);
+      const double rr = c->host_sc[S_RR];
+      if (!std::isfinite(rr)) {
+        st = HMG_ERR_NONFINITE;
+        break;
+      }
+      if (rr == 0.0) {  // exact solution
+        inf.converged = 1;
+        inf.rel_residual = 0.0;
+        st = HMG_OK;
+        break;
+      }
+      beta = std::sqrt(rr);
+      LAUNCH(c, HMG_K_ORTHO, 0, s, launch_normalise(L, c->gm_V, c->gm_V, c->red.sc + S_RR, s));
+    }
+  }
+  // true residual ||b - H^ x|| / ||b||
+  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s));
+  LAUNCH(c, HMG_K_RESID_SQ, 0, s, launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s));
+  cuda_ok(cudaEventRecord(c->ev1, s), "event");
+  read_scalars(c, s);
+  inf.true_rel_residual = bb > 0 ? std::sqrt(c->host_sc[S_TRUE] / bb) : 0.0;
+  float ms = 0.f;
+  cuda_ok(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event time");
+  inf.solve_ms = ms;
+  if (info) *info = inf;
+  return st;
+}
+
 void check_solve_params(const hmg_solve_params* p) {
   require(p != nullptr, "params is NULL");
   require(p->precision == HMG_PRECISION_FP64 || p->precision == HMG_PRECISION_MIXED, "bad precision");
-  require(p->krylov == HMG_KRYLOV_CG || p->krylov == HMG_KRYLOV_FCG, "bad krylov");
+  require(p->krylov == HMG_KRYLOV_CG || p->krylov == HMG_KRYLOV_FCG || p->krylov == HMG_KRYLOV_GMRES,
+          "bad krylov");
+  require(p->krylov != HMG_KRYLOV_GMRES || (p->restart >= 1 && p->restart <= GMRES_MAX_RESTART),
+          "GMRES restart must be in [1, " + std::to_string(GMRES_MAX_RESTART) + "]");
   require(p->rtol > 0.0 && p->rtol < 1.0, "rtol must be in (0, 1)");
   require(p->max_iter >= 1 && p->max_iter <= 100000, "max_iter must be in [1, 100000]");
   check_cycle_params(p->nu_pre, p->nu_post, p->n_coarse);
@@ -761,7 +974,7 @@ hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* 
 const char* hmg_kernel_name(int kernel) {
   static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",     "prolong",  "resid_restrict", "apply",
                                            "dot",    "update_xr", "update_p", "layout",         "resid_sq",
-                                           "assembly", "theta_grad"};
+                                           "assembly", "theta_grad", "ortho"};
   return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
 }
 

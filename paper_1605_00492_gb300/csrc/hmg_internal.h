@@ -28,6 +28,8 @@ constexpr int TW = 32;                 // columns per tile
 constexpr int SMALL_LEVEL_TILES = 152;  // levels with at most this many tiles are latency bound
 constexpr int FUSED_PROLONG_MAX_TILES = 160;  // FP64 levels up to this size fuse prolongation into the sweep
 constexpr int RED_MAX_BLOCKS = 16384;  // partial sums of one reduction (>= tiles of the finest level)
+constexpr int GMRES_MAX_RESTART = HMG_GMRES_MAX_RESTART;
+constexpr int GS_MAX_BLOCKS = 608;     // blocks of one Gram-Schmidt pass (4 per SM)
 
 struct HostLevel {
   int refinement = 0;
@@ -134,8 +136,30 @@ void launch_resid_sq(const Level& L, const double* b, const double* q, const Red
 void launch_check_finite(const Level& L, const double* v, const Reduce& red, cudaStream_t s);
 
 int reduce_grid(int64_t n);
+
+// GMRES (gmres.cu).  Basis vectors are contiguous FP64 tiled vectors, vector
+// i at V + i * ld; nv <= GMRES_MAX_RESTART.
+struct GsWork {
+  double* part = nullptr;       // (GMRES_MAX_RESTART + 1) * GS_MAX_BLOCKS block partials
+  unsigned int* counter = nullptr;
+  double* h = nullptr;          // GMRES_MAX_RESTART: first-pass coefficients
+  double* h2 = nullptr;         // GMRES_MAX_RESTART + 1: second-pass coefficients, then |w|^2
+  double* hn = nullptr;         // 1: h_(j+1,j)
+};
+void launch_gs_dots(const Level& L, const double* V, int64_t ld, int nv, const double* w, const GsWork& ws,
+                    cudaStream_t s);  // h = V^T w
+void launch_gs_update(const Level& L, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
+                      cudaStream_t s);  // w -= V h; h2 = V^T w, |w|^2
+void launch_gs_final(const Level& L, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
+                     cudaStream_t s);  // w -= V h2; w /= hn
+void launch_gmres_x(const Level& L, double* x, const double* Z, int64_t ld, int nv, const double* y,
+                    cudaStream_t s);  // x += Z y
+void launch_sub_norm(const Level& L, const double* b, const double* q, double* v, const Reduce& red,
+                     cudaStream_t s);  // v = b - q; s0 = |v|^2
+void launch_normalise(const Level& L, const double* a, double* v, const double* nrm2, cudaStream_t s);
 // FP64 -> FP32 (round to nearest even) or FP32 -> FP64 on the integer pipe
 void launch_convert(int64_t n, const void* src, int src_dt, void* dst, cudaStream_t s);
+
 
 }  // namespace hmg
 
@@ -178,7 +202,7 @@ struct hmg_ctx {
   int64_t launches = 0;
   // CUDA graphs of the Krylov iteration body, one per cycle configuration
   struct BodyGraph {
-    int key = -1;
+    int64_t key = -1;
     unsigned long long trace = 0;   // tracing masks the graph was captured with (0: none)
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;
@@ -186,4 +210,14 @@ struct hmg_ctx {
   };
   std::vector<BodyGraph> graphs;
   cudaStream_t capture_stream = nullptr;  // graphs are captured here, launched on the caller's stream
+
+  // GMRES workspace: basis V (gm_m + 1 vectors) and preconditioned
+  // directions Z (gm_m vectors), allocated by the first GMRES solve that
+  // needs them; gm_small holds h, h2, hn and the least-squares solution y.
+  int gm_m = 0;
+  double* gm_V = nullptr;
+  double* gm_Z = nullptr;
+  hmg::GsWork gm{};
+  double* gm_y = nullptr;
+  double* gm_host = nullptr;      // page-locked copy of gm_small
 };

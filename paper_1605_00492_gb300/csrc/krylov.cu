@@ -34,47 +34,111 @@ __global__ void k_to_column(int nc, int nz, int64_t Np, const T* __restrict__ ti
   if (decode(t, nz, nc, c, l)) col[(int64_t)c * nz + l] = tiled[t];
 }
 
+// The vector kernels below read and write two elements per access (16-byte
+// loads and stores; n is even for every tiled vector, since the padded column
+// count is a multiple of 32, and an odd last element is handled by thread 0).
+// Each grid-stride step covers 4 elements per thread, so that 4 independent
+// 16-byte loads per operand are in flight.
+
+inline __device__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
+inline __device__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+#define HMG_V2(p) reinterpret_cast<const double2*>(p)
+#define HMG_W2(p) reinterpret_cast<double2*>(p)
+
 // s0 = a.b, s1 = c.d (NV = 2)
 template <int NV>
 __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
                       const double* __restrict__ c, const double* __restrict__ d, Reduce red) {
-  double s0 = 0.0, s1 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    s0 = fma(a[i], b[i], s0);
-    if (NV == 2) s1 = fma(c[i], d[i], s1);
+  double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+  const int64_t n2 = n >> 1, st = gstride();
+  int64_t i = gtid();
+  for (; i + st < n2; i += 2 * st) {
+    const double2 a0 = HMG_V2(a)[i], b0 = HMG_V2(b)[i], a1 = HMG_V2(a)[i + st], b1 = HMG_V2(b)[i + st];
+    double2 c0, d0, c1, d1;
+    if (NV == 2) {
+      c0 = HMG_V2(c)[i];
+      d0 = HMG_V2(d)[i];
+      c1 = HMG_V2(c)[i + st];
+      d1 = HMG_V2(d)[i + st];
+    }
+    s0 = fma(a0.x, b0.x, s0);
+    t0 = fma(a0.y, b0.y, t0);
+    s0 = fma(a1.x, b1.x, s0);
+    t0 = fma(a1.y, b1.y, t0);
+    if (NV == 2) {
+      s1 = fma(c0.x, d0.x, s1);
+      t1 = fma(c0.y, d0.y, t1);
+      s1 = fma(c1.x, d1.x, s1);
+      t1 = fma(c1.y, d1.y, t1);
+    }
+  }
+  if (i < n2) {
+    const double2 a0 = HMG_V2(a)[i], b0 = HMG_V2(b)[i];
+    s0 = fma(a0.x, b0.x, s0);
+    t0 = fma(a0.y, b0.y, t0);
+    if (NV == 2) {
+      const double2 c0 = HMG_V2(c)[i], d0 = HMG_V2(d)[i];
+      s1 = fma(c0.x, d0.x, s1);
+      t1 = fma(c0.y, d0.y, t1);
+    }
+  }
+  if ((n & 1) && gtid() == 0) {
+    s0 = fma(a[n - 1], b[n - 1], s0);
+    if (NV == 2) s1 = fma(c[n - 1], d[n - 1], s1);
   }
   HMG_RED_SCRATCH(scratch);
-  grid_reduce<NV>(s0, s1, red, scratch);
+  grid_reduce<NV>(s0 + t0, s1 + t1, red, scratch);
 }
 
 // x += alpha p; r -= alpha q; s0 = r.r
 __global__ void k_update_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                             const double* __restrict__ p, const double* __restrict__ q, Reduce red) {
   const double alpha = red.sc[S_ALPHA];
-  double s0 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    s0 += ri * ri;
+  double s0 = 0.0, t0 = 0.0;
+  const int64_t n2 = n >> 1;
+  for (int64_t i = gtid(); i < n2; i += gstride()) {
+    double2 xi = HMG_V2(x)[i], ri = HMG_V2(r)[i];
+    const double2 pi = HMG_V2(p)[i], qi = HMG_V2(q)[i];
+    xi.x = fma(alpha, pi.x, xi.x);
+    xi.y = fma(alpha, pi.y, xi.y);
+    ri.x = fma(-alpha, qi.x, ri.x);
+    ri.y = fma(-alpha, qi.y, ri.y);
+    HMG_W2(x)[i] = xi;
+    HMG_W2(r)[i] = ri;
+    s0 = fma(ri.x, ri.x, s0);
+    t0 = fma(ri.y, ri.y, t0);
+  }
+  if ((n & 1) && gtid() == 0) {
+    x[n - 1] = fma(alpha, p[n - 1], x[n - 1]);
+    const double rl = fma(-alpha, q[n - 1], r[n - 1]);
+    r[n - 1] = rl;
+    s0 = fma(rl, rl, s0);
   }
   HMG_RED_SCRATCH(scratch);
-  grid_reduce<1>(s0, 0.0, red, scratch);
+  grid_reduce<1>(s0 + t0, 0.0, red, scratch);
 }
 
 // p = z + beta p
 __global__ void k_update_p(int64_t n, double* __restrict__ p, const double* __restrict__ z,
                            const double* __restrict__ sc) {
   const double beta = sc[S_BETA];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  const int64_t n2 = n >> 1;
+  for (int64_t i = gtid(); i < n2; i += gstride()) {
+    double2 pi = HMG_V2(p)[i];
+    const double2 zi = HMG_V2(z)[i];
+    pi.x = fma(beta, pi.x, zi.x);
+    pi.y = fma(beta, pi.y, zi.y);
+    HMG_W2(p)[i] = pi;
+  }
+  if ((n & 1) && gtid() == 0) p[n - 1] = fma(beta, p[n - 1], z[n - 1]);
 }
 
 // s0 = |b - q|^2
 __global__ void k_resid_sq(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
                            Reduce red) {
   double s0 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = gtid(); i < n; i += gstride()) {
     double v = b[i] - q[i];
     s0 += v * v;
   }

@@ -177,6 +177,22 @@ def test_solve_mixed_precision_error_against_oracle():
     assert rel_l2(c.host(x), x_ref[c.idx[0]]) < 1e-6
 
 
+@pytest.mark.parametrize("nz", [16, 32])
+def test_mixed_on_register_sweep_levels(nz):
+    # 20,480 columns = 640 tiles: the FP32 cycle's finest level takes the
+    # register-resident sweep and residual, the final sweep carrying the dots.
+    c = case(5, nz, 3)
+    b = gi.rhs(c.ops[0].ncells)
+    z_ref = multigrid.vcycle(c.ops, b)
+    z = c.h.vcycle(c.gpu(b), precision="mixed")
+    assert rel_l2(c.host(z), z_ref[c.idx[0]]) < 1e-4
+    x_ref, _ = krylov.pcg(c.ops[0].H.dot, lambda v: multigrid.vcycle(c.ops, v), b, rtol=1e-12)
+    for kind in ("cg", "fcg", "gmres"):
+        x, info = c.h.solve(c.gpu(b), precision="mixed", krylov=kind, rtol=1e-8)
+        assert info["converged"] == 1 and info["true_rel_residual"] < 2e-8, (kind, info)
+        assert rel_l2(c.host(x), x_ref[c.idx[0]]) < 1e-6, kind
+
+
 def test_solve_flexible_cg_fp64():
     c = case(3, 16, 3)
     b = gi.rhs(c.ops[0].ncells)
@@ -184,6 +200,55 @@ def test_solve_flexible_cg_fp64():
     x, info = c.h.solve(c.gpu(b), krylov="fcg", rtol=1e-8)
     assert abs(info["iterations"] - info_ref.iterations) <= 1
     assert rel_l2(c.host(x), x_ref[c.idx[0]]) <= 1e-9
+
+
+@pytest.mark.parametrize("restart", [30, 4, 1])
+def test_solve_gmres_fp64_matches_oracle(restart):
+    c = case(3, 16, 3)
+    b = gi.rhs(c.ops[0].ncells)
+    x_ref, info_ref = krylov.fgmres(c.ops[0].H.dot, lambda v: multigrid.vcycle(c.ops, v), b, rtol=1e-8,
+                                    restart=restart)
+    x, info = c.h.solve(c.gpu(b), krylov="gmres", restart=restart, rtol=1e-8)
+    assert info["converged"] == 1 and info["true_rel_residual"] < 2e-8
+    assert abs(info["iterations"] - info_ref.iterations) <= 1, (info, info_ref.iterations)
+    assert info["rel_residual"] == pytest.approx(info_ref.residuals[-1], rel=1e-3)
+    assert rel_l2(c.host(x), x_ref[c.idx[0]]) <= 1e-9
+
+
+def test_solve_gmres_fixed_steps_match_oracle_iterate():
+    """A fixed number of Arnoldi steps with no stopping (rtol tiny): the
+    iterate after 5 steps of GMRES(3) (a restart inside) against the
+    oracle's, element by element."""
+    c = case(2, 8, 2)
+    b = gi.rhs(c.ops[0].ncells)
+    x_ref, _ = krylov.fgmres(c.ops[0].H.dot, lambda v: multigrid.vcycle(c.ops, v), b, rtol=1e-300,
+                             max_iter=5, restart=3)
+    x, info = c.h.solve(c.gpu(b), krylov="gmres", restart=3, rtol=1e-300, max_iter=5, raise_on_failure=False)
+    assert info["status"] == "HMG_ERR_NOT_CONVERGED" and info["iterations"] == 5
+    assert rel_l2(c.host(x), x_ref[c.idx[0]]) <= 1e-10
+
+
+def test_solve_gmres_mixed_and_status_codes():
+    c = case(3, 16, 3)
+    b = gi.rhs(c.ops[0].ncells)
+    x_ref, _ = krylov.pcg(c.ops[0].H.dot, lambda v: multigrid.vcycle(c.ops, v), b, rtol=1e-12)
+    x, info = c.h.solve(c.gpu(b), precision="mixed", krylov="gmres", rtol=1e-8)
+    assert info["converged"] == 1 and info["true_rel_residual"] < 2e-8
+    assert rel_l2(c.host(x), x_ref[c.idx[0]]) < 1e-6
+    for bad in (0, 33):
+        with pytest.raises(hmg.HMGError) as e:
+            c.h.solve(c.gpu(b), krylov="gmres", restart=bad)
+        assert e.value.name == "HMG_ERR_INVALID_ARG"
+    bn = b.copy()
+    bn[5] = np.inf
+    _, info = c.h.solve(c.gpu(bn), krylov="gmres", raise_on_failure=False)
+    assert info["status"] == "HMG_ERR_NONFINITE"
+    x, info = c.h.solve(torch.zeros(c.ops[0].ncells, dtype=torch.float64, device=DEV), krylov="gmres")
+    assert info["converged"] == 1 and torch.count_nonzero(x) == 0
+    # a longer restart reallocates the basis; the solve after it still agrees
+    x2, _ = c.h.solve(c.gpu(b), krylov="gmres", restart=32, rtol=1e-8)
+    x3, _ = c.h.solve(c.gpu(b), krylov="gmres", restart=30, rtol=1e-8)
+    assert torch.equal(x2, x3)
 
 
 def test_solve_host_buffers():
