@@ -30,6 +30,7 @@ SEED_PSTAR = 1      # manufactured solution p* ~ N(0, 1)
 SEED_THETA = 2      # vertical-coupling coefficient field theta = exp(0.3 N(0,1))
 SEED_PTARGET = 3    # adjoint target p_target ~ N(0, 1)
 SEED_DIRS = 4       # finite-difference directions
+SEED_MIXED = 5      # velocity-pressure right-hand side (R_U, R_P) ~ N(0, 1)
 
 
 def ncolumns(refinement):
@@ -66,3 +67,10 @@ def ptarget(n, seed=SEED_PTARGET):
 def directions(n, count, seed=SEED_DIRS):
     """`count` iid N(0,1) direction vectors of length n, shape (count, n)."""
     return np.random.default_rng(seed).standard_normal((count, n))
+
+
+def mixed_rhs(nu, np_, seed=SEED_MIXED):
+    """Field values (R_U, R_P) of the velocity-pressure right-hand side: nu
+    face values, then np_ cell values, iid N(0,1) (faces in face order); the
+    system's right-hand side is (M2~ R_U, M3 R_P)."""
+    return normal(nu + np_, seed)

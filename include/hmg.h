@@ -90,6 +90,9 @@ typedef struct {
   int n_coarse;         /* smoother iterations on the coarsest level, >= 1 (2) */
   int restart;          /* GMRES restart length m, 1..HMG_GMRES_MAX_RESTART (30);
                            ignored by CG and FCG */
+  int levels;           /* multigrid levels used, 0 (all) or 1..nlevels; 1 is the
+                           single-level method of Sec. 6: n_coarse block-Jacobi
+                           vertical line relaxations on the finest level */
 } hmg_solve_params;
 
 typedef struct {

@@ -174,12 +174,25 @@ void prof_add(hmg_ctx* c, int kernel, int level, double ms) {
 
 struct CycleCfg {
   int nu_pre = 2, nu_post = 2, n_coarse = 2;
+  int nlev = 1;          // levels used: 0 .. nlev - 1 (nlev = 1: single-level line relaxation)
   bool mixed = false;
   double omega = 0.8;
 };
 
+CycleCfg make_cfg(const hmg_ctx* c, int nu_pre, int nu_post, int n_coarse, int levels, int precision) {
+  CycleCfg cfg;
+  cfg.nu_pre = nu_pre;
+  cfg.nu_post = nu_post;
+  cfg.n_coarse = n_coarse;
+  cfg.nlev = levels > 0 ? levels : (int)c->lv.size();
+  cfg.mixed = precision == HMG_PRECISION_MIXED;
+  cfg.omega = c->ph.omega;
+  return cfg;
+}
+
 int level_dt(const hmg_ctx* c, const CycleCfg& cfg, int lev) {
-  return (cfg.mixed && lev < (int)c->lv.size() - 1) ? HMG_FP32 : HMG_FP64;
+  (void)c;
+  return (cfg.mixed && lev < cfg.nlev - 1) ? HMG_FP32 : HMG_FP64;
 }
 
 void* work(Level& L, int dt, int which) {
@@ -193,7 +206,7 @@ void* work(Level& L, int dt, int which) {
 void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, void* out, int out_dt,
            cudaStream_t s, const SweepDot* dot = nullptr) {
   Level& L = c->lv[lev];
-  const int nlev = (int)c->lv.size();
+  const int nlev = cfg.nlev;
   const int dt = level_dt(c, cfg, lev);
   const bool coarsest = lev == nlev - 1;
   const int npre = coarsest ? cfg.n_coarse : cfg.nu_pre;
@@ -284,7 +297,8 @@ SweepDot beta_dot(const hmg_ctx* c, bool flexible) {
 // (holding their outputs for the dots costs the registers that let the
 // column recurrence run ahead of its loads).
 bool fused_beta(const hmg_ctx* c, const CycleCfg& cfg) {
-  return !cfg.mixed && (c->lv.size() > 1 || cfg.n_coarse > 1);
+  (void)c;
+  return !cfg.mixed && (cfg.nlev > 1 || cfg.n_coarse > 1);
 }
 
 void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
@@ -310,7 +324,8 @@ void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t
 // Arnoldi step j within a restart cycle (its vectors are baked in).
 int64_t graph_key(const CycleCfg& cfg, bool flexible, int gmres_step = -1) {
   const int64_t base =
-      ((((cfg.mixed ? 1 : 0) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 + cfg.nu_post) * 65 + cfg.n_coarse;
+      (((((cfg.mixed ? 1 : 0) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 + cfg.nu_post) * 65 + cfg.n_coarse) *
+          33 + cfg.nlev;
   return base * (GMRES_MAX_RESTART + 1) + (gmres_step + 1);
 }
 
@@ -380,12 +395,7 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
 hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
   if (p.krylov == HMG_KRYLOV_GMRES) return solve_gmres(c, p, info, s);
   Level& L = c->lv[0];
-  CycleCfg cfg;
-  cfg.nu_pre = p.nu_pre;
-  cfg.nu_post = p.nu_post;
-  cfg.n_coarse = p.n_coarse;
-  cfg.mixed = p.precision == HMG_PRECISION_MIXED;
-  cfg.omega = c->ph.omega;
+  const CycleCfg cfg = make_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
   const bool flexible = cfg.mixed || p.krylov == HMG_KRYLOV_FCG;
   const size_t bytes = (size_t)L.Np * sizeof(double);
   hmg_solve_info inf{};
@@ -514,12 +524,7 @@ void gmres_step(hmg_ctx* c, const CycleCfg& cfg, int j, cudaStream_t s) {
 
 hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
   Level& L = c->lv[0];
-  CycleCfg cfg;
-  cfg.nu_pre = p.nu_pre;
-  cfg.nu_post = p.nu_post;
-  cfg.n_coarse = p.n_coarse;
-  cfg.mixed = p.precision == HMG_PRECISION_MIXED;
-  cfg.omega = c->ph.omega;
+  const CycleCfg cfg = make_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
   const int m = p.restart;
   ensure_gmres(c, m);
   const int64_t ld = L.Np;
@@ -652,6 +657,7 @@ void check_solve_params(const hmg_solve_params* p) {
           "bad krylov");
   require(p->krylov != HMG_KRYLOV_GMRES || (p->restart >= 1 && p->restart <= GMRES_MAX_RESTART),
           "GMRES restart must be in [1, " + std::to_string(GMRES_MAX_RESTART) + "]");
+  require(p->levels >= 0, "levels must be >= 0");
   require(p->rtol > 0.0 && p->rtol < 1.0, "rtol must be in (0, 1)");
   require(p->max_iter >= 1 && p->max_iter <= 100000, "max_iter must be in [1, 100000]");
   check_cycle_params(p->nu_pre, p->nu_post, p->n_coarse);
@@ -881,12 +887,7 @@ hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r, vo
     check_cycle_params(nu_pre, nu_post, n_coarse);
     need_assembled(ctx);
     cudaStream_t s = as_stream(stream);
-    CycleCfg cfg;
-    cfg.nu_pre = nu_pre;
-    cfg.nu_post = nu_post;
-    cfg.n_coarse = n_coarse;
-    cfg.mixed = precision == HMG_PRECISION_MIXED;
-    cfg.omega = ctx->ph.omega;
+    const CycleCfg cfg = make_cfg(ctx, nu_pre, nu_post, n_coarse, 0, precision);
     Level& L = ctx->lv[0];
     if (layout == HMG_LAYOUT_TILED) {
       cycle(ctx, cfg, 0, r, HMG_FP64, z, HMG_FP64, s);
@@ -904,6 +905,7 @@ hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_p
   hmg_status result = HMG_OK;
   hmg_status st = guarded(ctx, [&] {
     check_solve_params(params);
+    require(params->levels <= (int)ctx->lv.size(), "levels exceeds the hierarchy's level count");
     require(b && x, "b and x must be non-NULL device pointers");
     need_assembled(ctx);
     cudaStream_t s = as_stream(stream);
@@ -926,6 +928,7 @@ hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host, co
   hmg_status result = HMG_OK;
   hmg_status st = guarded(ctx, [&] {
     check_solve_params(params);
+    require(params->levels <= (int)ctx->lv.size(), "levels exceeds the hierarchy's level count");
     require(b_host && x_host, "b_host and x_host must be non-NULL");
     need_assembled(ctx);
     cudaStream_t s = as_stream(stream);

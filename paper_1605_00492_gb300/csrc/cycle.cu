@@ -131,6 +131,13 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
       q2 = tile_base(nb.z >> 2, nz);
     }
   }
+  // Small levels (TW2) where one batch of RB rows per warp covers the column
+  // (nz <= RB * NW): phase A also loads w and u~ for phases B' and D, so the
+  // CTA waits for global memory once instead of three times.
+  const bool carry = TW2 && nz <= RB * NW;
+  T wc[RB], uc_c[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) wc[i] = uc_c[i] = 0;
   // A
   for (int l0 = warp; l0 < nz; l0 += RB * NW) {
     T bl[RB], lo[RB], a0[RB], a1[RB], a2[RB];
@@ -142,6 +149,13 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
         const int64_t o = (int64_t)l * TW;
         bl[i] = cvt<T>(b[base + o]);
         lo[i] = L.lo[base + o];
+        if (TW2 && carry) {
+          wc[i] = L.w[base + o];
+          if (MODE != MODE_ZERO) {
+            uc_c[i] = u[base + o];
+            if (MODE == MODE_PRO) uc_c[i] += cvt<T>(ec[q + o]);
+          }
+        }
         if (MODE != MODE_ZERO) {
           a0[i] = u[s0 + o];
           a1[i] = u[s1 + o];
@@ -262,7 +276,7 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
 #pragma unroll
       for (int i = 0; i < RB; ++i) {
         const int l = l0 + i * NW;
-        wv[i] = (l < nz) ? L.w[base + (int64_t)l * TW] : (T)0;
+        wv[i] = carry ? wc[i] : ((l < nz) ? L.w[base + (int64_t)l * TW] : (T)0);
       }
 #pragma unroll
       for (int i = 0; i < RB; ++i) {
@@ -297,7 +311,9 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
         for (int i = 0; i < RB; ++i) {
           const int l = l0 + i * NW;
           uc[i] = 0;
-          if (l < nz) {
+          if (carry) {
+            uc[i] = uc_c[i];
+          } else if (l < nz) {
             uc[i] = u[base + (int64_t)l * TW];
             if (MODE == MODE_PRO) uc[i] += cvt<T>(ec[q + (int64_t)l * TW]);
           }
@@ -629,24 +645,19 @@ k_tapply(LD<T> L, int ntiles, int RG, const T* __restrict__ x, T* __restrict__ y
   const int nz = L.nz;
   double acc[2] = {0.0, 0.0};  // alternate rows: no dependent FP64 chain
   for (int tile = blockIdx.x / RG; tile < ntiles; tile += gridDim.x / RG) {
+    // padding columns (levels under 32 columns) are their own neighbours with
+    // zero coefficients and data: their stencil is zero, so every lane runs
+    // the same branch-free row loop and y stays zero there
     const int c = tile * TW + lane;
-    const bool valid = c < L.nc;
     const int64_t base = (int64_t)tile * TW * nz + lane;
-    typename Vec4<T>::type g{};
-    int64_t s0 = 0, s1 = 0, s2 = 0;
-    if (valid) {
-      const int4 nb = L.nbr[c];
-      g = L.gh[c];
-      s0 = tile_base(nb.x, nz);
-      s1 = tile_base(nb.y, nz);
-      s2 = tile_base(nb.z, nz);
-    }
+    const int4 nb = L.nbr[c];
+    const typename Vec4<T>::type g = L.gh[c];
+    const int64_t s0 = tile_base(nb.x, nz), s1 = tile_base(nb.y, nz), s2 = tile_base(nb.z, nz);
     int k = 0;
-#pragma unroll 2
+#pragma unroll 4
     for (int l = row0; l < nz; l += rstep, ++k) {
       const int64_t t = base + (int64_t)l * TW;
-      T v = 0;
-      if (valid) v = stencil_acc<T, 1>(L, x, t, l, (T)0, g, s0, s1, s2);
+      const T v = stencil_acc<T, 1>(L, x, t, l, (T)0, g, s0, s1, s2);
       y[t] = v;
       if (DOT) acc[k & 1] = fma((double)x[t], (double)v, acc[k & 1]);
     }

@@ -251,6 +251,25 @@ def test_solve_gmres_mixed_and_status_codes():
     assert torch.equal(x2, x3)
 
 
+@pytest.mark.parametrize("krylov_kind", ["cg", "gmres"])
+def test_single_level_method_matches_oracle(krylov_kind):
+    """levels=1: two block-Jacobi vertical line relaxations as the
+    preconditioner (the single-level method of Sec. 6) on a 3-level context."""
+    c = case(3, 16, 3)
+    b = gi.rhs(c.ops[0].ncells)
+    P = lambda v: multigrid.vcycle(c.ops[:1], v)
+    solver = krylov.pcg if krylov_kind == "cg" else krylov.fgmres
+    x_ref, info_ref = solver(c.ops[0].H.dot, P, b, rtol=1e-8, max_iter=500)
+    x, info = c.h.solve(c.gpu(b), krylov=krylov_kind, levels=1, rtol=1e-8, max_iter=500)
+    assert info["converged"] == 1
+    assert abs(info["iterations"] - info_ref.iterations) <= 1, (info, info_ref.iterations)
+    assert rel_l2(c.host(x), x_ref[c.idx[0]]) <= 1e-9
+    _, info_mg = c.h.solve(c.gpu(b), krylov=krylov_kind, rtol=1e-8)
+    assert info["iterations"] > 2 * info_mg["iterations"]
+    with pytest.raises(hmg.HMGError):
+        c.h.solve(c.gpu(b), levels=4)
+
+
 def test_solve_host_buffers():
     c = case(3, 16, 3)
     b = gi.rhs(c.ops[0].ncells)[c.idx[0]]
@@ -366,3 +385,18 @@ def test_integer_pipe_conversions_match_hardware_bitwise():
     assert torch.equal(mine.view(torch.int32), hw.view(torch.int32))
     back = hmg.convert(hw, torch.float64)
     assert torch.equal(back.view(torch.int64), hw.to(torch.float64).view(torch.int64))
+
+
+def test_algorithmic_experiments_small():
+    """The experiment drivers run and show what Sec. 6 reports: multigrid
+    iteration counts that do not grow with resolution, and a single-level
+    method that needs several times as many iterations."""
+    from paper_1605_00492_gb300 import experiments
+    g = experiments.grid_independence([3, 4], nlayers=16)
+    assert all(row["true_rel_residual"] < 2e-8 for row in g)
+    assert g[1]["iterations"] <= g[0]["iterations"] + 1
+    c = experiments.cfl_sweep([8.0], refinement=3, nlayers=16, nlevels=3)
+    assert c[0]["single_level"]["iterations"] > 2 * c[0]["multigrid"]["iterations"]
+    hist = experiments.history(refinement=3, nlayers=16, nlevels=3)
+    mg = hist["multigrid"]
+    assert mg[-1] < 1e-8 and all(b < a for a, b in zip(mg, mg[1:]))
