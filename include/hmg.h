@@ -180,6 +180,38 @@ hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x,
 hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host,
                           const hmg_solve_params* params, hmg_solve_info* info, void* stream);
 
+/* The velocity-pressure system of Sec. 4.1 (Eq. PressureVelocitySystem) on
+ * the finest level, lowest order (RT0 x DG0, no orography):
+ *   A (U, P) = ( M2~ U - dt/2 D^T P ,  dt/2 c^2 D U + M3 P ),
+ *   M2~ = M2^h (+) (1 + w_N^2) M2^z  (full, not lumped, velocity mass),
+ * with unit-flux bases, the prism geometry of hmg_assemble_helmholtz and its
+ * parameters (c, N, nu_cfl, dx_m).  Vectors in COLUMN layouts:
+ *   U: horizontal faces e * nlayers + l (edge e of hmg_export_edges, layer l;
+ *      positive flux from column t into column tn), then vertical faces
+ *      c * (nlayers - 1) + l (between layers l and l + 1, positive upwards);
+ *   P: cells c * nlayers + l.
+ * Sizes from hmg_mixed_sizes.  The coefficient tables are built by the first
+ * call that needs them (device memory of about 9 vectors of ncells doubles,
+ * plus the GMRES basis of 2m + 1 vectors of the system's size). */
+hmg_status hmg_mixed_sizes(const hmg_ctx* ctx, int64_t* n_hfaces, int64_t* n_vfaces, int64_t* n_cells);
+
+/* edges[4 e + 0..3] = (t, k, tn, kn): edge e is local edge k (opposite vertex
+ * k) of column t and local edge kn of column tn, t < tn; edges are ordered by
+ * t, then k.  Host buffer of 4 * (n_hfaces / nlayers) int32. */
+hmg_status hmg_export_edges(hmg_ctx* ctx, int32_t* edges);
+
+/* (yu, yp) = A (u, p), device FP64 vectors.  Errors: INVALID_ARG, STATE, CUDA. */
+hmg_status hmg_mixed_apply(hmg_ctx* ctx, const double* u, const double* p, double* yu, double* yp, void* stream);
+
+/* Solve A (u, p) = (bu, bp) with restarted flexible GMRES(params->restart),
+ * x_0 = 0, preconditioned on the right by the Schur-complement factorisation
+ * of Sec. 4.2 (Eq. SchurComplement) with the diagonal velocity-mass inverse
+ * of Eq. LumpedMass and one V-cycle (params: precision, nu_pre, nu_post,
+ * n_coarse, levels) for H^^-1; stops when ||r|| / ||(bu, bp)|| < rtol (the
+ * paper uses 1e-5).  params->krylov is ignored.  Status as hmg_solve. */
+hmg_status hmg_mixed_solve(hmg_ctx* ctx, const double* bu, const double* bp, double* u, double* p,
+                           const hmg_solve_params* params, hmg_solve_info* info, void* stream);
+
 /* Adjoint face contraction: grad_theta_K = -lambda^T (dH^/dtheta_K) p for the
  * theta given to the last hmg_assemble_helmholtz (all ones if NULL).  Only
  * the vertical term of Eq. (Preconditioner) depends on theta, through the two

@@ -88,6 +88,11 @@ _SIGNATURES = {
     "hmg_solve": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
     "hmg_solve_host": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
     "hmg_theta_grad": [_P, _P, _P, _P, _P],
+    "hmg_mixed_sizes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int64)],
+    "hmg_export_edges": [_P, _P],
+    "hmg_mixed_apply": [_P, _P, _P, _P, _P, _P],
+    "hmg_mixed_solve": [_P, _P, _P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
     "hmg_to_layout": [_P, _I, _I, _P, _I, _P, _P],
     "hmg_sync": [_P, _P],
     "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
@@ -252,6 +257,47 @@ class Hierarchy:
         if raise_on_failure:
             self._check(st)
         return x_host, d
+
+    # ---- velocity-pressure system (Sec. 4.1) and its Schur-complement preconditioner (Sec. 4.2)
+
+    def mixed_sizes(self):
+        """(horizontal faces, vertical faces, cells) of the finest level."""
+        h, v, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.hmg_mixed_sizes(self._ctx, ctypes.byref(h), ctypes.byref(v), ctypes.byref(c)))
+        return h.value, v.value, c.value
+
+    def export_edges(self):
+        """(ne, 4) int32 array of (t, k, tn, kn) per edge."""
+        import numpy as np
+        nh, _, _ = self.mixed_sizes()
+        ne = nh // self.levels[0]["nlayers"]
+        e = np.zeros((ne, 4), dtype=np.int32)
+        self._check(self.lib.hmg_export_edges(self._ctx, e.ctypes.data_as(_P)))
+        return e
+
+    def mixed_apply(self, u, p, stream=None):
+        """(yu, yp) = A (u, p) for device FP64 tensors in the COLUMN layouts."""
+        yu, yp = torch.empty_like(u), torch.empty_like(p)
+        self._check(self.lib.hmg_mixed_apply(self._ctx, _ptr(u.contiguous()), _ptr(p.contiguous()), _ptr(yu), _ptr(yp),
+                                             _stream(stream)))
+        return yu, yp
+
+    def mixed_solve(self, bu, bp, stream=None, raise_on_failure=True, **kw):
+        """(u, p) = A^-1 (bu, bp) by GMRES(restart) with the Schur-complement
+        preconditioner; keyword arguments as solve (rtol defaults to 1e-5 here,
+        the paper's tolerance).  Returns (u, p, info dict)."""
+        kw.setdefault("rtol", 1e-5)
+        kw.setdefault("krylov", "gmres")
+        u, p = torch.empty_like(bu), torch.empty_like(bp)
+        info = SolveInfo()
+        prm = self.solve_params(**kw)
+        st = self.lib.hmg_mixed_solve(self._ctx, _ptr(bu.contiguous()), _ptr(bp.contiguous()), _ptr(u), _ptr(p),
+                                      ctypes.byref(prm), ctypes.byref(info), _stream(stream))
+        d = info.as_dict()
+        d["status"] = STATUS.get(st, st)
+        if raise_on_failure:
+            self._check(st)
+        return u, p, d
 
     def theta_grad(self, p, lam, out=None, stream=None):
         g = out if out is not None else torch.empty_like(p)

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <functional>
 #include <new>
 #include <string>
 
@@ -476,10 +477,10 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
 constexpr int GM_H = 0, GM_H2 = GMRES_MAX_RESTART, GM_HN = 2 * GMRES_MAX_RESTART + 1, GM_READ = GM_HN + 1,
               GM_Y = 3 * GMRES_MAX_RESTART, GM_SMALL = 4 * GMRES_MAX_RESTART;
 
-// Basis storage for restart length m (kept across solves; a longer restart
-// reallocates it and drops the graphs that hold the old vectors).
-void ensure_gmres(hmg_ctx* c, int m) {
-  Level& L = c->lv[0];
+// Basis storage for restart length m on vectors of n entries (kept across
+// solves; a longer restart or longer vectors reallocate it and drop the
+// graphs that hold the old vectors).
+void ensure_gmres(hmg_ctx* c, int m, int64_t n) {
   if (!c->gm_host) {
     double* small = dalloc<double>(c, GM_SMALL);
     c->gm.h = small + GM_H;
@@ -490,7 +491,7 @@ void ensure_gmres(hmg_ctx* c, int m) {
     c->gm.counter = dalloc<unsigned int>(c, 1);
     cuda_ok(cudaMallocHost(&c->gm_host, GM_SMALL * sizeof(double)), "cudaMallocHost");
   }
-  if (m <= c->gm_m) return;
+  if (m <= c->gm_m && n <= c->gm_n) return;
   for (auto& g : c->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     destroy_graph_prof(g.prof);
@@ -499,41 +500,58 @@ void ensure_gmres(hmg_ctx* c, int m) {
   dfree(c, c->gm_V);
   dfree(c, c->gm_Z);
   c->gm_V = c->gm_Z = nullptr;
+  const int mm = std::max(m, c->gm_m);
+  const int64_t nn = std::max(n, c->gm_n);
   c->gm_m = 0;
-  c->gm_V = dalloc<double>(c, (size_t)(m + 1) * L.Np);
-  c->gm_Z = dalloc<double>(c, (size_t)m * L.Np);
-  c->gm_m = m;
+  c->gm_n = 0;
+  c->gm_V = dalloc<double>(c, (size_t)(mm + 1) * nn);
+  c->gm_Z = dalloc<double>(c, (size_t)mm * nn);
+  c->gm_m = mm;
+  c->gm_n = nn;
 }
 
-// Arnoldi step j: z_j = V v_j, w = H^ z_j into v_(j+1), two Gram-Schmidt
+// A linear system for the GMRES driver: n entries per vector (tiled layouts,
+// padding entries zero), the right-hand side b and the iterate x (device),
+// y = A x and z = P^-1 r launched on a stream, and the graph key of its
+// first Arnoldi step (step j uses key + j; the top bits name the system).
+struct KrylovSystem {
+  int64_t n = 0;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double* tmp = nullptr;      // n entries of scratch
+  std::function<void(const double*, double*, cudaStream_t)> apply;
+  std::function<void(const double*, double*, cudaStream_t)> precond;
+  int64_t key = 0;
+};
+
+// Arnoldi step j: z_j = P^-1 v_j, w = A z_j into v_(j+1), two Gram-Schmidt
 // passes against v_0..v_j and the normalisation, results copied to the host.
-void gmres_step(hmg_ctx* c, const CycleCfg& cfg, int j, cudaStream_t s) {
-  Level& L = c->lv[0];
-  const int64_t ld = L.Np;
+void gmres_step(hmg_ctx* c, const KrylovSystem& sys, int j, cudaStream_t s) {
+  const int64_t ld = sys.n;
   double* vj = c->gm_V + j * ld;
   double* zj = c->gm_Z + j * ld;
   double* w = c->gm_V + (j + 1) * ld;
-  cycle(c, cfg, 0, vj, HMG_FP64, zj, HMG_FP64, s);
-  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, zj, w, nullptr, s));
-  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_dots(L, c->gm_V, ld, j + 1, w, c->gm, s));
-  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_update(L, c->gm_V, ld, j + 1, w, c->gm, s));
-  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_final(L, c->gm_V, ld, j + 1, w, c->gm, s));
+  sys.precond(vj, zj, s);
+  sys.apply(zj, w, s);
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_dots(ld, c->gm_V, ld, j + 1, w, c->gm, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_update(ld, c->gm_V, ld, j + 1, w, c->gm, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_final(ld, c->gm_V, ld, j + 1, w, c->gm, s));
   cuda_ok(cudaMemcpyAsync(c->gm_host, c->gm.h, GM_READ * sizeof(double), cudaMemcpyDeviceToHost, s),
           "GMRES read");
 }
 
-hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
-  Level& L = c->lv[0];
-  const CycleCfg cfg = make_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
+// Restarted flexible GMRES(m) with right preconditioning on `sys`, x_0 = 0.
+hmg_status gmres_run(hmg_ctx* c, const KrylovSystem& sys, const hmg_solve_params& p, hmg_solve_info* info,
+                     cudaStream_t s) {
   const int m = p.restart;
-  ensure_gmres(c, m);
-  const int64_t ld = L.Np;
+  const int64_t ld = sys.n;
+  ensure_gmres(c, m, ld);
   hmg_solve_info inf{};
 
   cuda_ok(cudaEventRecord(c->ev0, s), "event");
   cuda_ok(cudaMemsetAsync(c->red.sc, 0, S_COUNT * sizeof(double), s), "memset");
-  cuda_ok(cudaMemsetAsync(c->kx, 0, (size_t)ld * sizeof(double), s), "memset");
-  LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, c->kb, c->kb, nullptr, nullptr, red_with(c, EPI_STORE0, S_BB), s));
+  cuda_ok(cudaMemsetAsync(sys.x, 0, (size_t)ld * sizeof(double), s), "memset");
+  LAUNCH(c, HMG_K_DOT, 0, s, launch_dot_n(ld, sys.b, sys.b, red_with(c, EPI_STORE0, S_BB), s));
   read_scalars(c, s);
   const double bb = c->host_sc[S_BB];
   if (((int)c->host_sc[S_FLAG] & F_NONFINITE) || !std::isfinite(bb)) {
@@ -546,7 +564,7 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     st = HMG_OK;
   } else {
     const double r0 = std::sqrt(bb);
-    LAUNCH(c, HMG_K_ORTHO, 0, s, launch_normalise(L, c->kb, c->gm_V, c->red.sc + S_BB, s));
+    LAUNCH(c, HMG_K_ORTHO, 0, s, launch_normalise(ld, sys.b, c->gm_V, c->red.sc + S_BB, s));
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
     double beta = r0;
@@ -559,7 +577,7 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
       int jend = 0;
       for (int j = 0; j < m; ++j) {
         hmg_ctx::BodyGraph* gr =
-            run_graph(c, graph_key(cfg, true, j), [&](cudaStream_t cs) { gmres_step(c, cfg, j, cs); }, s);
+            run_graph(c, sys.key + j, [&](cudaStream_t cs) { gmres_step(c, sys, j, cs); }, s);
         cuda_ok(cudaStreamSynchronize(s), "solve");
         harvest_body(c, gr);
         const double* hh = c->gm_host;
@@ -575,9 +593,9 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
           break;
         }
         for (int i = 0; i < j; ++i) {  // earlier rotations on column j
-          const double a = Hij(i, j), b = Hij(i + 1, j);
-          Hij(i, j) = cs[i] * a + sn[i] * b;
-          Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+          const double a = Hij(i, j), bv = Hij(i + 1, j);
+          Hij(i, j) = cs[i] * a + sn[i] * bv;
+          Hij(i + 1, j) = -sn[i] * a + cs[i] * bv;
         }
         const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
         if (!(den > 0.0)) {
@@ -615,12 +633,12 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
         std::copy(y.begin(), y.begin() + jend, c->gm_host + GM_Y);
         cuda_ok(cudaMemcpyAsync(c->gm_y, c->gm_host + GM_Y, jend * sizeof(double), cudaMemcpyHostToDevice, s),
                 "GMRES y");
-        LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gmres_x(L, c->kx, c->gm_Z, ld, jend, c->gm_y, s));
+        LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gmres_x(ld, sys.x, c->gm_Z, ld, jend, c->gm_y, s));
       }
       if (stop) break;
-      // restart from the residual of the new iterate: v_0 = (b - H^ x) / beta
-      LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s));
-      LAUNCH(c, HMG_K_ORTHO, 0, s, launch_sub_norm(L, c->kb, c->kq, c->gm_V, red_with(c, EPI_STORE0, S_RR), s));
+      // restart from the residual of the new iterate: v_0 = (b - A x) / beta
+      sys.apply(sys.x, sys.tmp, s);
+      LAUNCH(c, HMG_K_ORTHO, 0, s, launch_sub_norm(ld, sys.b, sys.tmp, c->gm_V, red_with(c, EPI_STORE0, S_RR), s));
       read_scalars(c, s);
       const double rr = c->host_sc[S_RR];
       if (!std::isfinite(rr)) {
@@ -634,12 +652,12 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
         break;
       }
       beta = std::sqrt(rr);
-      LAUNCH(c, HMG_K_ORTHO, 0, s, launch_normalise(L, c->gm_V, c->gm_V, c->red.sc + S_RR, s));
+      LAUNCH(c, HMG_K_ORTHO, 0, s, launch_normalise(ld, c->gm_V, c->gm_V, c->red.sc + S_RR, s));
     }
   }
-  // true residual ||b - H^ x|| / ||b||
-  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s));
-  LAUNCH(c, HMG_K_RESID_SQ, 0, s, launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s));
+  // true residual ||b - A x|| / ||b||
+  sys.apply(sys.x, sys.tmp, s);
+  LAUNCH(c, HMG_K_RESID_SQ, 0, s, launch_sub_norm(ld, sys.b, sys.tmp, sys.tmp, red_with(c, EPI_STORE0, S_TRUE), s));
   cuda_ok(cudaEventRecord(c->ev1, s), "event");
   read_scalars(c, s);
   inf.true_rel_residual = bb > 0 ? std::sqrt(c->host_sc[S_TRUE] / bb) : 0.0;
@@ -648,6 +666,113 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   inf.solve_ms = ms;
   if (info) *info = inf;
   return st;
+}
+
+// GMRES(m) on H^ x = b (tiled kb, kx), preconditioned by the V-cycle.
+hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  Level& L = c->lv[0];
+  const CycleCfg cfg = make_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
+  KrylovSystem sys;
+  sys.n = L.Np;
+  sys.b = c->kb;
+  sys.x = c->kx;
+  sys.tmp = c->kq;
+  sys.apply = [c, &L](const double* x, double* y, cudaStream_t st) {
+    LAUNCH(c, HMG_K_APPLY, 0, st, launch_apply(L, HMG_FP64, x, y, nullptr, st));
+  };
+  sys.precond = [c, cfg](const double* r, double* z, cudaStream_t st) {
+    cycle(c, cfg, 0, r, HMG_FP64, z, HMG_FP64, st);
+  };
+  sys.key = (1LL << 60) + graph_key(cfg, true, 0);
+  return gmres_run(c, sys, p, info, s);
+}
+
+// ------------------------------------------------------------ velocity-pressure system
+
+// Edge list (t, k, tn, kn with t < tn, ordered by t then k), per-column edge
+// table and the coefficient arrays of the finest level; built on first use.
+void mixed_edges_host(hmg_ctx* c, std::vector<int4>* cedge_out) {
+  MixedSys& M = c->mx;
+  const Level& L = c->lv[0];
+  const std::vector<int32_t>& nbr = L.nbr_host;
+  std::vector<int32_t> edges;
+  std::vector<int4> cedge(L.ncp, make_int4(0, 0, 0, 0));
+  for (int t = 0; t < L.nc; ++t)
+    for (int k = 0; k < 3; ++k) {
+      const int tn = nbr[3 * t + k];
+      if (t < tn) {
+        int kn = 0;
+        while (kn < 3 && nbr[3 * tn + kn] != t) ++kn;
+        require(kn < 3, "mesh neighbours are not symmetric");
+        const int e = (int)(edges.size() / 4);
+        edges.insert(edges.end(), {t, k, tn, kn});
+        int* ct = &cedge[t].x;
+        ct[k] = e;
+        int* cn = &cedge[tn].x;
+        cn[kn] = e;
+        cedge[tn].w |= 1 << kn;   // -1 on the higher-numbered column
+      }
+    }
+  M.ne = (int)(edges.size() / 4);
+  M.nep = (M.ne + TW - 1) / TW * TW;
+  M.nh = (int64_t)M.nep * L.nz;
+  M.n = M.nh + 2 * L.Np;
+  M.edges_host = edges;
+  if (cedge_out) cedge_out->swap(cedge);
+}
+
+void ensure_mixed(hmg_ctx* c, cudaStream_t s) {
+  MixedSys& M = c->mx;
+  if (M.ready) return;
+  const Level& L = c->lv[0];
+  std::vector<int4> cedge;
+  mixed_edges_host(c, &cedge);
+  const std::vector<int32_t>& edges = M.edges_host;
+  std::vector<int4> ed(M.nep, make_int4(0, 0, 0, 0));
+  for (int e = 0; e < M.ne; ++e) ed[e] = make_int4(edges[4 * e], edges[4 * e + 1], edges[4 * e + 2], edges[4 * e + 3]);
+  M.edge = dalloc<int4>(c, M.nep);
+  M.enb = dalloc<int4>(c, M.nep);
+  M.ecoef = dalloc<double4_32a>(c, M.nep);
+  M.emass = dalloc<double>(c, M.nep);
+  M.cedge = dalloc<int4>(c, L.ncp);
+  M.zd = dalloc<double>(c, L.Np);
+  M.m3 = dalloc<double>(c, L.Np);
+  M.b = dalloc<double>(c, M.n);
+  M.x = dalloc<double>(c, M.n);
+  M.t1 = dalloc<double>(c, M.n);
+  M.t2 = dalloc<double>(c, M.n);
+  cuda_ok(cudaMemcpy(M.edge, ed.data(), ed.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
+  cuda_ok(cudaMemcpy(M.cedge, cedge.data(), cedge.size() * sizeof(int4), cudaMemcpyHostToDevice), "upload");
+  Phys geo;   // geometry only: the coefficients do not depend on the operator parameters
+  geo.R = c->mp.radius_m;
+  geo.dz = c->mp.thickness_m / c->mp.nlayers;
+  LAUNCHN(c, HMG_K_ASSEMBLY, 0, s, 2, launch_mixed_coeffs(L, M, geo, s));
+  cuda_ok(cudaStreamSynchronize(s), "mixed setup");
+  M.ready = true;
+}
+
+// GMRES(m) on the velocity-pressure system (tiled mx.b, mx.x) with the
+// Schur-complement preconditioner; H^^-1 is one V-cycle of the given form.
+hmg_status solve_mixed_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  Level& L = c->lv[0];
+  MixedSys& M = c->mx;
+  const CycleCfg cfg = make_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
+  const int64_t off_p = M.nh + L.Np;   // cell part of a vector
+  KrylovSystem sys;
+  sys.n = M.n;
+  sys.b = M.b;
+  sys.x = M.x;
+  sys.tmp = M.t1;
+  sys.apply = [c, &L, &M](const double* x, double* y, cudaStream_t st) {
+    LAUNCH(c, HMG_K_APPLY, 0, st, launch_mixed_apply(L, M, c->ph, x, y, st));
+  };
+  sys.precond = [c, &L, &M, cfg, off_p](const double* r, double* z, cudaStream_t st) {
+    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mixed_pre_lower(L, M, c->ph, r, M.t2, st));
+    cycle(c, cfg, 0, M.t2, HMG_FP64, z + off_p, HMG_FP64, st);
+    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mixed_pre_upper(L, M, c->ph, r, z, st));
+  };
+  sys.key = (2LL << 60) + graph_key(cfg, true, 0);
+  return gmres_run(c, sys, p, info, s);
 }
 
 void check_solve_params(const hmg_solve_params* p) {
@@ -834,6 +959,9 @@ hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const do
     ph.wc2 = wc * wc;
     ph.vfac = wc * wc / (1.0 + wn * wn);
     ph.omega = p->omega;
+    ph.a = 0.5 * dt;
+    ph.c2 = p->c * p->c;
+    ph.wn2 = wn * wn;
     ctx->has_theta = theta != nullptr;
     if (theta) {
       LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(ctx->lv[0], HMG_FP64, theta, ctx->lv[0].theta, s));
@@ -941,6 +1069,68 @@ hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host, co
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
   if (st != HMG_OK) return st;
+  return result;
+}
+
+hmg_status hmg_mixed_sizes(const hmg_ctx* ctx, int64_t* n_hfaces, int64_t* n_vfaces, int64_t* n_cells) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  const Level& L = ctx->lv[0];
+  const int64_t ne = (int64_t)L.nc * 3 / 2;
+  if (n_hfaces) *n_hfaces = ne * L.nz;
+  if (n_vfaces) *n_vfaces = (int64_t)L.nc * (L.nz - 1);
+  if (n_cells) *n_cells = L.N;
+  return HMG_OK;
+}
+
+hmg_status hmg_export_edges(hmg_ctx* ctx, int32_t* edges) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(edges != nullptr, "edges is NULL");
+    if (ctx->mx.edges_host.empty()) mixed_edges_host(ctx, nullptr);
+    std::memcpy(edges, ctx->mx.edges_host.data(), ctx->mx.edges_host.size() * sizeof(int32_t));
+  });
+}
+
+hmg_status hmg_mixed_apply(hmg_ctx* ctx, const double* u, const double* p, double* yu, double* yp, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(u && p && yu && yp, "u, p, yu and yp must be non-NULL device pointers");
+    require(u != yu && p != yp, "outputs must differ from inputs");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_mixed(ctx, s);
+    Level& L = ctx->lv[0];
+    MixedSys& M = ctx->mx;
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, true, u, p, M.t1, nullptr, nullptr, s));
+    LAUNCH(ctx, HMG_K_APPLY, 0, s, launch_mixed_apply(L, M, ctx->ph, M.t1, M.t2, s));
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, false, nullptr, nullptr, M.t2, yu, yp, s));
+  });
+}
+
+hmg_status hmg_mixed_solve(hmg_ctx* ctx, const double* bu, const double* bp, double* u, double* p,
+                           const hmg_solve_params* params, hmg_solve_info* info, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  hmg_status result = HMG_OK;
+  hmg_status st = guarded(ctx, [&] {
+    check_solve_params(params);
+    require(params->levels <= (int)ctx->lv.size(), "levels exceeds the hierarchy's level count");
+    require(params->restart >= 1 && params->restart <= GMRES_MAX_RESTART,
+            "GMRES restart must be in [1, " + std::to_string(GMRES_MAX_RESTART) + "]");
+    require(bu && bp && u && p, "bu, bp, u and p must be non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_mixed(ctx, s);
+    Level& L = ctx->lv[0];
+    MixedSys& M = ctx->mx;
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, true, bu, bp, M.b, nullptr, nullptr, s));
+    result = solve_mixed_tiled(ctx, *params, info, s);
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, false, nullptr, nullptr, M.x, u, p, s));
+    cuda_ok(cudaStreamSynchronize(s), "solve");
+  });
+  if (st != HMG_OK) return st;
+  if (result == HMG_ERR_NOT_CONVERGED) ctx->err = "maximum number of iterations reached";
+  if (result == HMG_ERR_BREAKDOWN) ctx->err = "GMRES breakdown";
+  if (result == HMG_ERR_NONFINITE) ctx->err = "non-finite residual";
   return result;
 }
 

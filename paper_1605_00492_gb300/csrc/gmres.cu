@@ -174,6 +174,15 @@ __global__ void k_sub_norm(int64_t n, const double* __restrict__ b, const double
   grid_reduce<1>(s0, 0.0, red, scratch);
 }
 
+// s0 = a.b over n entries
+__global__ void k_dot_n(int64_t n, const double* __restrict__ a, const double* __restrict__ b, Reduce red) {
+  double s0 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s0 = fma(a[i], b[i], s0);
+  HMG_RED_SCRATCH(scratch);
+  grid_reduce<1>(s0, 0.0, red, scratch);
+}
+
 // v = a / sqrt(*nrm2)  (a may be v)
 __global__ void k_normalise(int64_t n, const double* a, double* v, const double* __restrict__ nrm2) {
   const double s = 1.0 / sqrt(*nrm2);
@@ -187,53 +196,55 @@ int gs_blocks(int64_t n) {
 }
 
 template <int MAXV>
-void gs_launch(int which, const Level& L, const double* V, int64_t ld, int nv, double* w, const double* h,
+void gs_launch(int which, int64_t n, const double* V, int64_t ld, int nv, double* w, const double* h,
                const GsWork& ws, cudaStream_t s) {
-  const int g = gs_blocks(L.Np);
+  const int g = gs_blocks(n);
   switch (which) {
-    case 0: k_gs_dots<MAXV><<<g, GS_THREADS, 0, s>>>(L.Np, V, ld, nv, w, ws.part, ws.counter, ws.h); break;
-    case 1: k_gs_update<MAXV><<<g, GS_THREADS, 0, s>>>(L.Np, V, ld, nv, w, ws.h, ws.part, ws.counter, ws.h2); break;
-    case 2: k_gs_final<MAXV><<<g, GS_THREADS, 0, s>>>(L.Np, V, ld, nv, w, ws.h2, ws.hn); break;
-    default: k_gmres_x<MAXV><<<g, GS_THREADS, 0, s>>>(L.Np, w, V, ld, nv, h); break;
+    case 0: k_gs_dots<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, w, ws.part, ws.counter, ws.h); break;
+    case 1: k_gs_update<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, w, ws.h, ws.part, ws.counter, ws.h2); break;
+    case 2: k_gs_final<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, w, ws.h2, ws.hn); break;
+    default: k_gmres_x<MAXV><<<g, GS_THREADS, 0, s>>>(n, w, V, ld, nv, h); break;
   }
 }
 
-void gs_dispatch(int which, const Level& L, const double* V, int64_t ld, int nv, double* w, const double* h,
+void gs_dispatch(int which, int64_t n, const double* V, int64_t ld, int nv, double* w, const double* h,
                  const GsWork& ws, cudaStream_t s) {
-  if (nv <= 8) gs_launch<8>(which, L, V, ld, nv, w, h, ws, s);
-  else if (nv <= 16) gs_launch<16>(which, L, V, ld, nv, w, h, ws, s);
-  else gs_launch<GMRES_MAX_RESTART>(which, L, V, ld, nv, w, h, ws, s);
+  if (nv <= 8) gs_launch<8>(which, n, V, ld, nv, w, h, ws, s);
+  else if (nv <= 16) gs_launch<16>(which, n, V, ld, nv, w, h, ws, s);
+  else gs_launch<GMRES_MAX_RESTART>(which, n, V, ld, nv, w, h, ws, s);
 }
 
 }  // namespace
 
-void launch_gs_dots(const Level& L, const double* V, int64_t ld, int nv, const double* w, const GsWork& ws,
+void launch_gs_dots(int64_t n, const double* V, int64_t ld, int nv, const double* w, const GsWork& ws,
                     cudaStream_t s) {
-  gs_dispatch(0, L, V, ld, nv, const_cast<double*>(w), nullptr, ws, s);
+  gs_dispatch(0, n, V, ld, nv, const_cast<double*>(w), nullptr, ws, s);
 }
 
-void launch_gs_update(const Level& L, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
+void launch_gs_update(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
                       cudaStream_t s) {
-  gs_dispatch(1, L, V, ld, nv, w, nullptr, ws, s);
+  gs_dispatch(1, n, V, ld, nv, w, nullptr, ws, s);
 }
 
-void launch_gs_final(const Level& L, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
+void launch_gs_final(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
                      cudaStream_t s) {
-  gs_dispatch(2, L, V, ld, nv, w, nullptr, ws, s);
+  gs_dispatch(2, n, V, ld, nv, w, nullptr, ws, s);
 }
 
-void launch_gmres_x(const Level& L, double* x, const double* Z, int64_t ld, int nv, const double* y,
-                    cudaStream_t s) {
-  gs_dispatch(3, L, Z, ld, nv, x, y, GsWork{}, s);
+void launch_gmres_x(int64_t n, double* x, const double* Z, int64_t ld, int nv, const double* y, cudaStream_t s) {
+  gs_dispatch(3, n, Z, ld, nv, x, y, GsWork{}, s);
 }
 
-void launch_sub_norm(const Level& L, const double* b, const double* q, double* v, const Reduce& red,
-                     cudaStream_t s) {
-  k_sub_norm<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, b, q, v, red);
+void launch_sub_norm(int64_t n, const double* b, const double* q, double* v, const Reduce& red, cudaStream_t s) {
+  k_sub_norm<<<reduce_grid(n), 256, 0, s>>>(n, b, q, v, red);
 }
 
-void launch_normalise(const Level& L, const double* a, double* v, const double* nrm2, cudaStream_t s) {
-  k_normalise<<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, a, v, nrm2);
+void launch_normalise(int64_t n, const double* a, double* v, const double* nrm2, cudaStream_t s) {
+  k_normalise<<<reduce_grid(n), 256, 0, s>>>(n, a, v, nrm2);
+}
+
+void launch_dot_n(int64_t n, const double* a, const double* b, const Reduce& red, cudaStream_t s) {
+  k_dot_n<<<reduce_grid(n), 256, 0, s>>>(n, a, b, red);
 }
 
 }  // namespace hmg

@@ -94,7 +94,37 @@ struct Reduce {
 
 struct Phys {
   double R = 0, dz = 0, wc2 = 0, vfac = 0, omega = 0.8;
+  double a = 0, c2 = 0, wn2 = 0;   // dt / 2, c^2, w_N^2 (velocity-pressure system)
 };
+
+// The velocity-pressure system of the finest level (mixed.cu).  Vectors hold
+// [horizontal faces | vertical faces | cells]: horizontal faces tiled like
+// cells with edges in place of columns ((e / 32) * 32 * nz + l * 32 + e % 32,
+// nep = edges padded to 32); vertical faces in the cell tiling, row l being
+// the face between layers l and l + 1 (row nz - 1 zero); cells tiled.
+struct MixedSys {
+  bool ready = false;
+  int ne = 0, nep = 0;
+  int64_t nh = 0, n = 0;              // nep * nz; nh + 2 * Np
+  std::vector<int32_t> edges_host;    // ne x (t, k, tn, kn), t < tn
+  int4* edge = nullptr;               // nep: t, k, tn, kn
+  int4* enb = nullptr;                // nep: the four coupled edges
+  double4_32a* ecoef = nullptr;       // nep: their M2^h entries
+  double* emass = nullptr;            // nep: M2^h diagonal
+  int4* cedge = nullptr;              // ncp: edges of local edges 0..2, sign bits in w
+  double* zd = nullptr;               // Np: dz / (3 A_K)
+  double* m3 = nullptr;               // Np: |K|
+  double *b = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr;   // n entries each
+};
+void launch_mixed_coeffs(const Level& L, const MixedSys& M, const Phys& ph, cudaStream_t s);
+void launch_mixed_apply(const Level& L, const MixedSys& M, const Phys& ph, const double* x, double* y,
+                        cudaStream_t s);
+void launch_mixed_pre_lower(const Level& L, const MixedSys& M, const Phys& ph, const double* r, double* rp,
+                            cudaStream_t s);  // rp = r_P - a c^2 D M2inv r_U
+void launch_mixed_pre_upper(const Level& L, const MixedSys& M, const Phys& ph, const double* r, double* z,
+                            cudaStream_t s);  // z_U = M2inv (r_U + a D^T z_P)
+void launch_mixed_layout(const Level& L, const MixedSys& M, bool to_tiled, const double* u_col, const double* p_col,
+                         double* tiled, double* u_out, double* p_out, cudaStream_t s);
 
 // ---- assembly (assemble.cu)
 void launch_geometry(const Level& L, cudaStream_t s);
@@ -146,17 +176,18 @@ struct GsWork {
   double* h2 = nullptr;         // GMRES_MAX_RESTART + 1: second-pass coefficients, then |w|^2
   double* hn = nullptr;         // 1: h_(j+1,j)
 };
-void launch_gs_dots(const Level& L, const double* V, int64_t ld, int nv, const double* w, const GsWork& ws,
+void launch_gs_dots(int64_t n, const double* V, int64_t ld, int nv, const double* w, const GsWork& ws,
                     cudaStream_t s);  // h = V^T w
-void launch_gs_update(const Level& L, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
+void launch_gs_update(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
                       cudaStream_t s);  // w -= V h; h2 = V^T w, |w|^2
-void launch_gs_final(const Level& L, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
+void launch_gs_final(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
                      cudaStream_t s);  // w -= V h2; w /= hn
-void launch_gmres_x(const Level& L, double* x, const double* Z, int64_t ld, int nv, const double* y,
+void launch_gmres_x(int64_t n, double* x, const double* Z, int64_t ld, int nv, const double* y,
                     cudaStream_t s);  // x += Z y
-void launch_sub_norm(const Level& L, const double* b, const double* q, double* v, const Reduce& red,
+void launch_sub_norm(int64_t n, const double* b, const double* q, double* v, const Reduce& red,
                      cudaStream_t s);  // v = b - q; s0 = |v|^2
-void launch_normalise(const Level& L, const double* a, double* v, const double* nrm2, cudaStream_t s);
+void launch_normalise(int64_t n, const double* a, double* v, const double* nrm2, cudaStream_t s);
+void launch_dot_n(int64_t n, const double* a, const double* b, const Reduce& red, cudaStream_t s);  // s0 = a.b
 // FP64 -> FP32 (round to nearest even) or FP32 -> FP64 on the integer pipe
 void launch_convert(int64_t n, const void* src, int src_dt, void* dst, cudaStream_t s);
 
@@ -215,9 +246,12 @@ struct hmg_ctx {
   // directions Z (gm_m vectors), allocated by the first GMRES solve that
   // needs them; gm_small holds h, h2, hn and the least-squares solution y.
   int gm_m = 0;
+  int64_t gm_n = 0;               // entries per basis vector
   double* gm_V = nullptr;
   double* gm_Z = nullptr;
   hmg::GsWork gm{};
   double* gm_y = nullptr;
   double* gm_host = nullptr;      // page-locked copy of gm_small
+
+  hmg::MixedSys mx;               // velocity-pressure system, set up by its first use
 };
