@@ -52,6 +52,11 @@ ORACLE_ITERATIONS = 11
 FP64_PEAK_TFLOPS = 152 * 4 * 32 / 64 * 2 * 2.07e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 REFERENCE_BUDGET_S = 150.0   # wall time of the --impl reference timed + warm-up steps
+# DRAM bytes per launch of the dominant kernel class of the r6x64 bench (FP64
+# sweeps on the finest level: two plain sweeps and one with the fused r.z per
+# V-cycle), from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# of this bench command: 192.9, 191.4 and 190.4 MB (plain), 192.6 MB (with the dot)
+TRAFFIC_SWEEP_L0_R6X64 = 192.0e6
 
 
 def measured_peaks():
@@ -420,7 +425,8 @@ def run_gpu(args):
                 "frac": round(gbs / hbm, 4), "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     roof.update({"kernel": f"{dom_k}@level{dom_l}", "launches": cnt, "avg_us": round(avg_ms * 1e3, 2),
                  "bytes_per_launch": int(per_cell_b * n_l), "flops_per_launch": int(KERNEL_FLOPS[dom_k] * n_l),
-                 "traffic": args.traffic})
+                 "traffic": args.traffic if args.traffic is not None else
+                 (TRAFFIC_SWEEP_L0_R6X64 if (args.workload == "r6x64" and (dom_k, dom_l) == ("sweep", 0)) else None)})
 
     def breakdown(br):
         return {f"{k}@{lvl}": {"launches": c, "ms": round(t, 3)} for (k, lvl), (c, t) in sorted(br.items())}

@@ -93,6 +93,8 @@ typedef struct {
   int levels;           /* multigrid levels used, 0 (all) or 1..nlevels; 1 is the
                            single-level method of Sec. 6: n_coarse block-Jacobi
                            vertical line relaxations on the finest level */
+  int orth;             /* GMRES orthogonalisation: 0 or 1 = classical Gram-Schmidt
+                           once (as PETSc's GMRES does by default), 2 = twice */
 } hmg_solve_params;
 
 typedef struct {
@@ -164,7 +166,7 @@ hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r,
  * one V-cycle per iteration, x_0 = 0 (Sec. 5): CG (H^ is symmetric positive
  * definite), flexible CG, or restarted GMRES(m), the paper's outer method, in
  * its flexible right-preconditioned form (Saad, Algorithm 9.6: Arnoldi with
- * classical Gram-Schmidt applied twice, Givens rotations, the iterate formed
+ * classical Gram-Schmidt once or twice (params->orth), Givens rotations, the iterate formed
  * at the end of each restart cycle, stopping on the least-squares residual
  * ||r_k|| / ||b|| < rtol).  GMRES keeps 2m + 1 finest-level FP64 vectors,
  * allocated by the first GMRES solve that needs them.  b, x: FP64 device

@@ -49,7 +49,8 @@ class OpParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("krylov", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
-                ("n_coarse", ctypes.c_int), ("restart", ctypes.c_int), ("levels", ctypes.c_int)]
+                ("n_coarse", ctypes.c_int), ("restart", ctypes.c_int), ("levels", ctypes.c_int),
+                ("orth", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -227,9 +228,9 @@ class Hierarchy:
         return z
 
     def solve_params(self, precision="fp64", krylov="cg", rtol=1e-8, max_iter=500, nu_pre=2, nu_post=2,
-                     n_coarse=2, restart=30, levels=0):
+                     n_coarse=2, restart=30, levels=0, orth=1):
         return SolveParams(PRECISION[precision], KRYLOV[krylov], rtol, max_iter, nu_pre, nu_post, n_coarse,
-                           restart, levels)
+                           restart, levels, orth)
 
     def solve(self, b, out=None, stream=None, raise_on_failure=True, **kw):
         """x = H^^-1 b by V-cycle-preconditioned CG, flexible CG or GMRES(restart); returns (x, info dict)."""

@@ -522,6 +522,7 @@ struct KrylovSystem {
   std::function<void(const double*, double*, cudaStream_t)> apply;
   std::function<void(const double*, double*, cudaStream_t)> precond;
   int64_t key = 0;
+  int orth = 1;               // classical Gram-Schmidt passes: 1 or 2
 };
 
 // Arnoldi step j: z_j = P^-1 v_j, w = A z_j into v_(j+1), two Gram-Schmidt
@@ -533,9 +534,10 @@ void gmres_step(hmg_ctx* c, const KrylovSystem& sys, int j, cudaStream_t s) {
   double* w = c->gm_V + (j + 1) * ld;
   sys.precond(vj, zj, s);
   sys.apply(zj, w, s);
+  const int nd2 = sys.orth == 2 ? j + 1 : 0;
   LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_dots(ld, c->gm_V, ld, j + 1, w, c->gm, s));
-  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_update(ld, c->gm_V, ld, j + 1, w, c->gm, s));
-  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_final(ld, c->gm_V, ld, j + 1, w, c->gm, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_update(ld, c->gm_V, ld, j + 1, nd2 > 0, w, c->gm, s));
+  LAUNCH(c, HMG_K_ORTHO, 0, s, launch_gs_final(ld, c->gm_V, ld, nd2, w, c->gm, s));
   cuda_ok(cudaMemcpyAsync(c->gm_host, c->gm.h, GM_READ * sizeof(double), cudaMemcpyDeviceToHost, s),
           "GMRES read");
 }
@@ -581,9 +583,10 @@ hmg_status gmres_run(hmg_ctx* c, const KrylovSystem& sys, const hmg_solve_params
         cuda_ok(cudaStreamSynchronize(s), "solve");
         harvest_body(c, gr);
         const double* hh = c->gm_host;
-        bool finite = std::isfinite(hh[GM_HN]) && std::isfinite(hh[GM_H2 + j + 1]);
+        const int nd2 = sys.orth == 2 ? j + 1 : 0;
+        bool finite = std::isfinite(hh[GM_HN]) && std::isfinite(hh[GM_H2 + nd2]);
         for (int i = 0; i <= j; ++i) {
-          Hij(i, j) = hh[GM_H + i] + hh[GM_H2 + i];
+          Hij(i, j) = hh[GM_H + i] + (i < nd2 ? hh[GM_H2 + i] : 0.0);
           finite = finite && std::isfinite(Hij(i, j));
         }
         Hij(j + 1, j) = hh[GM_HN];
@@ -683,7 +686,8 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   sys.precond = [c, cfg](const double* r, double* z, cudaStream_t st) {
     cycle(c, cfg, 0, r, HMG_FP64, z, HMG_FP64, st);
   };
-  sys.key = (1LL << 60) + graph_key(cfg, true, 0);
+  sys.orth = p.orth == 2 ? 2 : 1;
+  sys.key = (1LL << 60) + (sys.orth == 2 ? (1LL << 59) : 0) + graph_key(cfg, true, 0);
   return gmres_run(c, sys, p, info, s);
 }
 
@@ -734,9 +738,11 @@ void ensure_mixed(hmg_ctx* c, cudaStream_t s) {
   M.enb = dalloc<int4>(c, M.nep);
   M.ecoef = dalloc<double4_32a>(c, M.nep);
   M.emass = dalloc<double>(c, M.nep);
+  M.einv = dalloc<double>(c, M.nep);
   M.cedge = dalloc<int4>(c, L.ncp);
   M.zd = dalloc<double>(c, L.Np);
   M.m3 = dalloc<double>(c, L.Np);
+  M.zsi = dalloc<double>(c, L.Np);
   M.b = dalloc<double>(c, M.n);
   M.x = dalloc<double>(c, M.n);
   M.t1 = dalloc<double>(c, M.n);
@@ -764,14 +770,15 @@ hmg_status solve_mixed_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_in
   sys.x = M.x;
   sys.tmp = M.t1;
   sys.apply = [c, &L, &M](const double* x, double* y, cudaStream_t st) {
-    LAUNCH(c, HMG_K_APPLY, 0, st, launch_mixed_apply(L, M, c->ph, x, y, st));
+    LAUNCHN(c, HMG_K_APPLY, 0, st, 2, launch_mixed_apply(L, M, c->ph, x, y, st));
   };
   sys.precond = [c, &L, &M, cfg, off_p](const double* r, double* z, cudaStream_t st) {
     LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mixed_pre_lower(L, M, c->ph, r, M.t2, st));
     cycle(c, cfg, 0, M.t2, HMG_FP64, z + off_p, HMG_FP64, st);
-    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mixed_pre_upper(L, M, c->ph, r, z, st));
+    LAUNCHN(c, HMG_K_ORTHO, 0, st, 2, launch_mixed_pre_upper(L, M, c->ph, r, z, st));
   };
-  sys.key = (2LL << 60) + graph_key(cfg, true, 0);
+  sys.orth = p.orth == 2 ? 2 : 1;
+  sys.key = (2LL << 60) + (sys.orth == 2 ? (1LL << 59) : 0) + graph_key(cfg, true, 0);
   return gmres_run(c, sys, p, info, s);
 }
 
@@ -783,6 +790,7 @@ void check_solve_params(const hmg_solve_params* p) {
   require(p->krylov != HMG_KRYLOV_GMRES || (p->restart >= 1 && p->restart <= GMRES_MAX_RESTART),
           "GMRES restart must be in [1, " + std::to_string(GMRES_MAX_RESTART) + "]");
   require(p->levels >= 0, "levels must be >= 0");
+  require(p->orth >= 0 && p->orth <= 2, "orth must be 0, 1 or 2");
   require(p->rtol > 0.0 && p->rtol < 1.0, "rtol must be in (0, 1)");
   require(p->max_iter >= 1 && p->max_iter <= 100000, "max_iter must be in [1, 100000]");
   check_cycle_params(p->nu_pre, p->nu_post, p->n_coarse);
@@ -1101,9 +1109,9 @@ hmg_status hmg_mixed_apply(hmg_ctx* ctx, const double* u, const double* p, doubl
     ensure_mixed(ctx, s);
     Level& L = ctx->lv[0];
     MixedSys& M = ctx->mx;
-    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, true, u, p, M.t1, nullptr, nullptr, s));
-    LAUNCH(ctx, HMG_K_APPLY, 0, s, launch_mixed_apply(L, M, ctx->ph, M.t1, M.t2, s));
-    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, false, nullptr, nullptr, M.t2, yu, yp, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, true, u, p, M.t1, nullptr, nullptr, s));
+    LAUNCHN(ctx, HMG_K_APPLY, 0, s, 2, launch_mixed_apply(L, M, ctx->ph, M.t1, M.t2, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, false, nullptr, nullptr, M.t2, yu, yp, s));
   });
 }
 
@@ -1122,9 +1130,9 @@ hmg_status hmg_mixed_solve(hmg_ctx* ctx, const double* bu, const double* bp, dou
     ensure_mixed(ctx, s);
     Level& L = ctx->lv[0];
     MixedSys& M = ctx->mx;
-    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, true, bu, bp, M.b, nullptr, nullptr, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, true, bu, bp, M.b, nullptr, nullptr, s));
     result = solve_mixed_tiled(ctx, *params, info, s);
-    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_mixed_layout(L, M, false, nullptr, nullptr, M.x, u, p, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, false, nullptr, nullptr, M.x, u, p, s));
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
   if (st != HMG_OK) return st;

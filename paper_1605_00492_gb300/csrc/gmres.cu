@@ -1,15 +1,16 @@
 // Vector kernels of the restarted flexible GMRES(m) outer solve (Sec. 5 wraps
 // the multigrid preconditioner in GMRES(30); flexible form: Saad, Iterative
 // Methods for Sparse Linear Systems, Algorithm 9.6).  The Arnoldi vector
-// w = H^ z_j is orthogonalised against v_0..v_j by classical Gram-Schmidt
-// applied twice, in three passes over the basis:
+// w = A z_j is orthogonalised against v_0..v_j by classical Gram-Schmidt,
+// once (the default of the PETSc GMRES the paper used) or twice, in three
+// passes over the basis:
 //
 //   k_gs_dots    h   = V^T w
-//   k_gs_update  w  -= V h;        h2 = V^T w, |w|^2 from the same pass
-//   k_gs_final   w  -= V h2;       v_(j+1) = w / h_(j+1,j)
+//   k_gs_update  w  -= V h;        |w|^2 (and, applied twice, h2 = V^T w) from the same pass
+//   k_gs_final   (twice: w -= V h2;)  v_(j+1) = w / h_(j+1,j)
 //
 // where h_(j+1,j)^2 = |w|^2 - |h2|^2 (Pythagoras: w after the second
-// projection is orthogonal to the basis to rounding).  Every dot product is
+// projection is orthogonal to the basis to rounding; |w|^2 once).  Every dot product is
 // a deterministic two-level reduction (fixed order within and across blocks)
 // whose last block writes the results.  Vectors are the finest level's tiled
 // FP64 vectors; the basis vectors are contiguous, vector i at V + i * ld.
@@ -70,50 +71,77 @@ __device__ __forceinline__ void multi_reduce(const double (&acc)[MAXV + 1], int 
   }
 }
 
+// Each thread takes U elements per grid-stride step (elements e0 + u * stride),
+// so that U independent loads per vector are in flight: with one element per
+// step the passes are bound by memory latency, not bandwidth.
+__host__ __device__ constexpr int gs_unroll(int maxv) { return maxv <= 8 ? 4 : (maxv <= 16 ? 2 : 1); }
+
 // out[i] = v_i . w, i < nv
 template <int MAXV>
 __global__ void __launch_bounds__(GS_THREADS)
 k_gs_dots(int64_t n, const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w,
           double* part, unsigned* counter, double* out) {
+  constexpr int U = gs_unroll(MAXV);
   double acc[MAXV + 1];
 #pragma unroll
   for (int v = 0; v <= MAXV; ++v) acc[v] = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e < n; e += (int64_t)gridDim.x * GS_THREADS) {
-    const double we = w[e];
+  const int64_t stride = (int64_t)gridDim.x * GS_THREADS;
+  for (int64_t e0 = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e0 < n; e0 += stride * U) {
+    double we[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) we[u] = (e0 + u * stride < n) ? w[e0 + u * stride] : 0.0;
 #pragma unroll
     for (int v = 0; v < MAXV; ++v)
-      if (v < nv) acc[v] = fma(V[v * ld + e], we, acc[v]);
+      if (v < nv) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < n) acc[v] = fma(V[v * ld + e0 + u * stride], we[u], acc[v]);
+      }
   }
   multi_reduce<MAXV>(acc, nv, false, part, counter, out);
 }
 
-// w -= sum_i h[i] v_i; out[i] = v_i . w (i < nv), out[nv] = w . w
+// w -= sum_i h[i] v_i; out[i] = v_i . w (i < nd2: the second pass of the
+// twice-applied form, nd2 = nv; 0 for the single pass), out[nd2] = w . w
 template <int MAXV>
 __global__ void __launch_bounds__(GS_THREADS)
-k_gs_update(int64_t n, const double* __restrict__ V, int64_t ld, int nv, double* __restrict__ w,
+k_gs_update(int64_t n, const double* __restrict__ V, int64_t ld, int nv, int nd2, double* __restrict__ w,
             const double* __restrict__ h, double* part, unsigned* counter, double* out) {
+  constexpr int U = gs_unroll(MAXV);
   __shared__ double hs[MAXV];
   if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
   double acc[MAXV + 1];
 #pragma unroll
   for (int v = 0; v <= MAXV; ++v) acc[v] = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e < n; e += (int64_t)gridDim.x * GS_THREADS) {
-    double ve[MAXV];
-    double we = w[e];
+  const int64_t stride = (int64_t)gridDim.x * GS_THREADS;
+  for (int64_t e0 = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e0 < n; e0 += stride * U) {
+    double we[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) we[u] = (e0 + u * stride < n) ? w[e0 + u * stride] : 0.0;
 #pragma unroll
     for (int v = 0; v < MAXV; ++v)
       if (v < nv) {
-        ve[v] = V[v * ld + e];
-        we = fma(-hs[v], ve[v], we);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < n) we[u] = fma(-hs[v], V[v * ld + e0 + u * stride], we[u]);
       }
-    w[e] = we;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * stride < n) {
+        w[e0 + u * stride] = we[u];
+        acc[MAXV] = fma(we[u], we[u], acc[MAXV]);
+      }
+    // the second projection's dots (twice-applied form) re-read the basis from cache
 #pragma unroll
     for (int v = 0; v < MAXV; ++v)
-      if (v < nv) acc[v] = fma(ve[v], we, acc[v]);
-    acc[MAXV] = fma(we, we, acc[MAXV]);
+      if (v < nd2) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < n) acc[v] = fma(V[v * ld + e0 + u * stride], we[u], acc[v]);
+      }
   }
-  multi_reduce<MAXV>(acc, nv, true, part, counter, out);
+  multi_reduce<MAXV>(acc, nd2, true, part, counter, out);
 }
 
 // w -= sum_i h2[i] v_i, then w /= hn with hn^2 = nrm2 - |h2|^2 (0 if not
@@ -123,6 +151,7 @@ template <int MAXV>
 __global__ void __launch_bounds__(GS_THREADS)
 k_gs_final(int64_t n, const double* __restrict__ V, int64_t ld, int nv, double* __restrict__ w,
            const double* __restrict__ h2, double* hn_out) {
+  constexpr int U = gs_unroll(MAXV);
   __shared__ double hs[MAXV];
   __shared__ double inv;
   if (threadIdx.x < nv) hs[threadIdx.x] = h2[threadIdx.x];
@@ -135,12 +164,21 @@ k_gs_final(int64_t n, const double* __restrict__ V, int64_t ld, int nv, double* 
   }
   __syncthreads();
   const double sc = inv;
-  for (int64_t e = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e < n; e += (int64_t)gridDim.x * GS_THREADS) {
-    double we = w[e];
+  const int64_t stride = (int64_t)gridDim.x * GS_THREADS;
+  for (int64_t e0 = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e0 < n; e0 += stride * U) {
+    double we[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) we[u] = (e0 + u * stride < n) ? w[e0 + u * stride] : 0.0;
 #pragma unroll
     for (int v = 0; v < MAXV; ++v)
-      if (v < nv) we = fma(-hs[v], V[v * ld + e], we);
-    w[e] = we * sc;
+      if (v < nv) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < n) we[u] = fma(-hs[v], V[v * ld + e0 + u * stride], we[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * stride < n) w[e0 + u * stride] = we[u] * sc;
   }
 }
 
@@ -149,15 +187,25 @@ template <int MAXV>
 __global__ void __launch_bounds__(GS_THREADS)
 k_gmres_x(int64_t n, double* __restrict__ x, const double* __restrict__ Z, int64_t ld, int nv,
           const double* __restrict__ y) {
+  constexpr int U = gs_unroll(MAXV);
   __shared__ double ys[MAXV];
   if (threadIdx.x < nv) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
-  for (int64_t e = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e < n; e += (int64_t)gridDim.x * GS_THREADS) {
-    double xe = x[e];
+  const int64_t stride = (int64_t)gridDim.x * GS_THREADS;
+  for (int64_t e0 = blockIdx.x * (int64_t)GS_THREADS + threadIdx.x; e0 < n; e0 += stride * U) {
+    double xe[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xe[u] = (e0 + u * stride < n) ? x[e0 + u * stride] : 0.0;
 #pragma unroll
     for (int v = 0; v < MAXV; ++v)
-      if (v < nv) xe = fma(ys[v], Z[v * ld + e], xe);
-    x[e] = xe;
+      if (v < nv) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < n) xe[u] = fma(ys[v], Z[v * ld + e0 + u * stride], xe[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * stride < n) x[e0 + u * stride] = xe[u];
   }
 }
 
@@ -201,7 +249,8 @@ void gs_launch(int which, int64_t n, const double* V, int64_t ld, int nv, double
   const int g = gs_blocks(n);
   switch (which) {
     case 0: k_gs_dots<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, w, ws.part, ws.counter, ws.h); break;
-    case 1: k_gs_update<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, w, ws.h, ws.part, ws.counter, ws.h2); break;
+    case 1: k_gs_update<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, nv, w, ws.h, ws.part, ws.counter, ws.h2); break;
+    case 4: k_gs_update<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, 0, w, ws.h, ws.part, ws.counter, ws.h2); break;
     case 2: k_gs_final<MAXV><<<g, GS_THREADS, 0, s>>>(n, V, ld, nv, w, ws.h2, ws.hn); break;
     default: k_gmres_x<MAXV><<<g, GS_THREADS, 0, s>>>(n, w, V, ld, nv, h); break;
   }
@@ -221,9 +270,9 @@ void launch_gs_dots(int64_t n, const double* V, int64_t ld, int nv, const double
   gs_dispatch(0, n, V, ld, nv, const_cast<double*>(w), nullptr, ws, s);
 }
 
-void launch_gs_update(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
-                      cudaStream_t s) {
-  gs_dispatch(1, n, V, ld, nv, w, nullptr, ws, s);
+void launch_gs_update(int64_t n, const double* V, int64_t ld, int nv, bool second_dots, double* w,
+                      const GsWork& ws, cudaStream_t s) {
+  gs_dispatch(second_dots ? 1 : 4, n, V, ld, nv, w, nullptr, ws, s);
 }
 
 void launch_gs_final(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,

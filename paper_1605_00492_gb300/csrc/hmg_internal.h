@@ -29,7 +29,7 @@ constexpr int SMALL_LEVEL_TILES = 152;  // levels with at most this many tiles a
 constexpr int FUSED_PROLONG_MAX_TILES = 160;  // FP64 levels up to this size fuse prolongation into the sweep
 constexpr int RED_MAX_BLOCKS = 16384;  // partial sums of one reduction (>= tiles of the finest level)
 constexpr int GMRES_MAX_RESTART = HMG_GMRES_MAX_RESTART;
-constexpr int GS_MAX_BLOCKS = 608;     // blocks of one Gram-Schmidt pass (4 per SM)
+constexpr int GS_MAX_BLOCKS = 1216;    // blocks of one Gram-Schmidt pass (8 per SM)
 
 struct HostLevel {
   int refinement = 0;
@@ -111,9 +111,11 @@ struct MixedSys {
   int4* enb = nullptr;                // nep: the four coupled edges
   double4_32a* ecoef = nullptr;       // nep: their M2^h entries
   double* emass = nullptr;            // nep: M2^h diagonal
+  double* einv = nullptr;             // nep: its reciprocal
   int4* cedge = nullptr;              // ncp: edges of local edges 0..2, sign bits in w
   double* zd = nullptr;               // Np: dz / (3 A_K)
   double* m3 = nullptr;               // Np: |K|
+  double* zsi = nullptr;              // Np: 1 / M2^z diagonal of the face above the cell
   double *b = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr;   // n entries each
 };
 void launch_mixed_coeffs(const Level& L, const MixedSys& M, const Phys& ph, cudaStream_t s);
@@ -173,13 +175,13 @@ struct GsWork {
   double* part = nullptr;       // (GMRES_MAX_RESTART + 1) * GS_MAX_BLOCKS block partials
   unsigned int* counter = nullptr;
   double* h = nullptr;          // GMRES_MAX_RESTART: first-pass coefficients
-  double* h2 = nullptr;         // GMRES_MAX_RESTART + 1: second-pass coefficients, then |w|^2
+  double* h2 = nullptr;         // GMRES_MAX_RESTART + 1: second-pass coefficients (if any), then |w|^2
   double* hn = nullptr;         // 1: h_(j+1,j)
 };
 void launch_gs_dots(int64_t n, const double* V, int64_t ld, int nv, const double* w, const GsWork& ws,
                     cudaStream_t s);  // h = V^T w
-void launch_gs_update(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
-                      cudaStream_t s);  // w -= V h; h2 = V^T w, |w|^2
+void launch_gs_update(int64_t n, const double* V, int64_t ld, int nv, bool second_dots, double* w,
+                      const GsWork& ws, cudaStream_t s);  // w -= V h; |w|^2 (second_dots: h2 = V^T w first)
 void launch_gs_final(int64_t n, const double* V, int64_t ld, int nv, double* w, const GsWork& ws,
                      cudaStream_t s);  // w -= V h2; w /= hn
 void launch_gmres_x(int64_t n, double* x, const double* Z, int64_t ld, int nv, const double* y,

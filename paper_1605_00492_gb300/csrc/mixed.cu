@@ -55,13 +55,13 @@ __device__ __forceinline__ int cedge_k(const int4& ce, int k) { return k == 0 ? 
 // Per edge: M2^h diagonal and the four coupled edges with their entries.
 __global__ void k_mx_edge_coeffs(int ne, int nep, double dz, const int4* __restrict__ edge,
                                  const int4* __restrict__ cedge, const double* __restrict__ verts, int4* enb,
-                                 double4_32a* ecoef, double* emass) {
+                                 double4_32a* ecoef, double* emass, double* einv) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nep) return;
   if (e >= ne) {
     enb[e] = make_int4(e, e, e, e);
     ecoef[e] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    emass[e] = 0.0;
+    emass[e] = einv[e] = 0.0;
     return;
   }
   const int4 ed = edge[e];
@@ -76,230 +76,243 @@ __global__ void k_mx_edge_coeffs(int ne, int nep, double dz, const int4* __restr
   ecoef[e] = make_double4_32a(csign(ct, k1) * St[k][k1] / dz, csign(ct, k2) * St[k][k2] / dz,
                               -csign(cn, kn1) * Sn[kn][kn1] / dz, -csign(cn, kn2) * Sn[kn][kn2] / dz);
   emass[e] = (St[k][k] + Sn[kn][kn]) / dz;
+  einv[e] = 1.0 / emass[e];
 }
 
-// Per cell: zd = dz / (3 A_K), m3 = |K| (prism reading: A_K = A1 rho_l^2)
+// Per cell: zd = dz / (3 A_K), m3 = |K| (prism reading: A_K = A1 rho_l^2),
+// and for the vertical face above the cell zsi = 1 / (zd_l + zd_(l+1)), the
+// reciprocal of its M2^z diagonal (0 at the top)
 __global__ void k_mx_cell_coeffs(int nc, int nz, int64_t Np, double R, double dz, const double* __restrict__ A1,
-                                 double* zd, double* m3) {
+                                 double* zd, double* m3, double* zsi) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= Np) return;
   const int lane = (int)(t & 31);
   const int l = (int)((t >> 5) % nz);
   const int c = (int)((t / (TW * nz)) * TW + lane);
   if (c >= nc) {
-    zd[t] = m3[t] = 0.0;
+    zd[t] = m3[t] = zsi[t] = 0.0;
     return;
   }
-  const double rho = R + (l + 0.5) * dz;
-  const double A = A1[c] * rho * rho;
+  const double rho = R + (l + 0.5) * dz, rhou = R + (l + 1.5) * dz;
+  const double A = A1[c] * rho * rho, Au = A1[c] * rhou * rhou;
   zd[t] = dz / (3.0 * A);
   m3[t] = A * dz;
+  zsi[t] = l < nz - 1 ? 1.0 / (dz / (3.0 * A) + dz / (3.0 * Au)) : 0.0;
 }
 
 struct MxArgs {
-  int nc, nz, ne;
+  int nc, nz, ne, ntc, nte;   // columns, layers, edges, column tiles, edge tiles
   int64_t Np, nh;
   double a, c2, wn2;
   const int4* edge;
   const int4* enb;
   const double4_32a* ecoef;
   const double* emass;
+  const double* einv;         // 1 / emass
   const int4* cedge;
   const double* zd;
   const double* m3;
+  const double* zsi;          // 1 / (zd_l + zd_(l+1))
+  double inv1wn2;             // 1 / (1 + w_N^2)
 };
 
-__device__ __forceinline__ void decode_h(int64_t t, int nz, int& e, int& l) {
-  e = (int)((t / (TW * nz)) * TW + (t & 31));
-  l = (int)((t >> 5) % nz);
-}
-__device__ __forceinline__ void decode_c(int64_t t, int nz, int& c, int& l) {
-  c = (int)((t / (TW * nz)) * TW + (t & 31));
-  l = (int)((t >> 5) % nz);
-}
+// 1 / M2~ diagonal of the vertical face between layers l and l + 1 (t = its index)
+__device__ __forceinline__ double mz_inv(const MxArgs& A, int64_t t) { return A.zsi[t] * A.inv1wn2; }
 
-// M2~ diagonal of the vertical face between layers l and l + 1 of column c (t = its index)
-__device__ __forceinline__ double mz_diag(const MxArgs& A, int64_t t) {
-  return (1.0 + A.wn2) * (A.zd[t] + A.zd[t + TW]);
-}
+// The kernels walk (tile, row) pairs without index division: CTAs stride over
+// tiles, warps over rows, lanes are the tile's 32 edges or columns.
+constexpr int MX_THREADS = 256;   // 8 warps: rows of a tile
+constexpr int MX_WARPS = MX_THREADS / 32;
 
-// y = A x, three sweeps over the parts of the vector
-__global__ void k_mx_apply(MxArgs A, const double* __restrict__ x, double* __restrict__ y) {
-  const double* xh = x;
-  const double* xz = x + A.nh;
+// Rows are unrolled by four so that each thread has several rows' loads in flight.
+#define MX_TILE_LOOP(NT)                                                                          \
+  for (int tile = blockIdx.x; tile < (NT); tile += gridDim.x)                                     \
+    _Pragma("unroll 4") for (int l = threadIdx.x >> 5; l < A.nz; l += MX_WARPS)
+
+// y_h = M2^h x_h - a D_h^T x_p
+__global__ void k_mx_apply_h(MxArgs A, const double* __restrict__ x, double* __restrict__ y) {
   const double* xp = x + A.nh + A.Np;
-  const int64_t n = A.nh + 2 * A.Np;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  MX_TILE_LOOP(A.nte) {
+    const int e = tile * TW + lane;
+    const int64_t i = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
     double v = 0.0;
-    if (i < A.nh) {
-      int e, l;
-      decode_h(i, A.nz, e, l);
-      if (e < A.ne) {
-        const int4 ed = A.edge[e];
-        const int4 nb = A.enb[e];
-        const double4_32a m = A.ecoef[e];
-        const int64_t o = (int64_t)l * TW;
-        v = A.emass[e] * xh[i];
-        v = fma(m.x, xh[tb(nb.x, A.nz) + o], v);
-        v = fma(m.y, xh[tb(nb.y, A.nz) + o], v);
-        v = fma(m.z, xh[tb(nb.z, A.nz) + o], v);
-        v = fma(m.w, xh[tb(nb.w, A.nz) + o], v);
-        v = fma(-A.a, xp[tb(ed.x, A.nz) + o] - xp[tb(ed.z, A.nz) + o], v);
-      }
-    } else if (i < A.nh + A.Np) {
-      const int64_t t = i - A.nh;
-      int c, l;
-      decode_c(t, A.nz, c, l);
-      if (c < A.nc && l < A.nz - 1) {
-        double m = (A.zd[t] + A.zd[t + TW]) * xz[t];
-        if (l > 0) m = fma(0.5 * A.zd[t], xz[t - TW], m);
-        if (l + 1 < A.nz - 1) m = fma(0.5 * A.zd[t + TW], xz[t + TW], m);
-        v = fma(1.0 + A.wn2, m, -A.a * (xp[t] - xp[t + TW]));
-      }
-    } else {
-      const int64_t t = i - A.nh - A.Np;
-      int c, l;
-      decode_c(t, A.nz, c, l);
-      if (c < A.nc) {
-        const int4 ce = A.cedge[c];
-        const int64_t o = (int64_t)l * TW;
-        double div = csign(ce, 0) * xh[tb(ce.x, A.nz) + o] + csign(ce, 1) * xh[tb(ce.y, A.nz) + o] +
-                     csign(ce, 2) * xh[tb(ce.z, A.nz) + o];
-        if (l < A.nz - 1) div += xz[t];
-        if (l > 0) div -= xz[t - TW];
-        v = fma(A.a * A.c2, div, A.m3[t] * xp[t]);
-      }
+    if (e < A.ne) {
+      const int4 ed = A.edge[e];
+      const int4 nb = A.enb[e];
+      const double4_32a m = A.ecoef[e];
+      const int64_t o = (int64_t)l * TW;
+      v = A.emass[e] * x[i];
+      v = fma(m.x, x[tb(nb.x, A.nz) + o], v);
+      v = fma(m.y, x[tb(nb.y, A.nz) + o], v);
+      v = fma(m.z, x[tb(nb.z, A.nz) + o], v);
+      v = fma(m.w, x[tb(nb.w, A.nz) + o], v);
+      v = fma(-A.a, xp[tb(ed.x, A.nz) + o] - xp[tb(ed.z, A.nz) + o], v);
     }
     y[i] = v;
   }
 }
 
-// rp = r_P - a c^2 D (M2inv r_U), written to the cell part of z
+// y_z = (1 + w_N^2) M2^z x_z - a D_z^T x_p;  y_p = a c^2 D x_u + M3 x_p
+__global__ void k_mx_apply_zp(MxArgs A, const double* __restrict__ x, double* __restrict__ y) {
+  const double* xh = x;
+  const double* xz = x + A.nh;
+  const double* xp = x + A.nh + A.Np;
+  const int lane = threadIdx.x & 31;
+  MX_TILE_LOOP(A.ntc) {
+    const int c = tile * TW + lane;
+    const int64_t t = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
+    double vz = 0.0, vp = 0.0;
+    if (c < A.nc) {
+      const int64_t o = (int64_t)l * TW;
+      if (l < A.nz - 1) {
+        double m = (A.zd[t] + A.zd[t + TW]) * xz[t];
+        if (l > 0) m = fma(0.5 * A.zd[t], xz[t - TW], m);
+        if (l + 1 < A.nz - 1) m = fma(0.5 * A.zd[t + TW], xz[t + TW], m);
+        vz = fma(1.0 + A.wn2, m, -A.a * (xp[t] - xp[t + TW]));
+      }
+      const int4 ce = A.cedge[c];
+      double div = csign(ce, 0) * xh[tb(ce.x, A.nz) + o] + csign(ce, 1) * xh[tb(ce.y, A.nz) + o] +
+                   csign(ce, 2) * xh[tb(ce.z, A.nz) + o];
+      if (l < A.nz - 1) div += xz[t];
+      if (l > 0) div -= xz[t - TW];
+      vp = fma(A.a * A.c2, div, A.m3[t] * xp[t]);
+    }
+    y[A.nh + t] = vz;
+    y[A.nh + A.Np + t] = vp;
+  }
+}
+
+// rp = r_P - a c^2 D (M2inv r_U)
 __global__ void k_mx_pre_lower(MxArgs A, const double* __restrict__ r, double* __restrict__ rp) {
   const double* rh = r;
   const double* rz = r + A.nh;
   const double* rpin = r + A.nh + A.Np;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.Np; t += (int64_t)gridDim.x * blockDim.x) {
-    int c, l;
-    decode_c(t, A.nz, c, l);
+  const int lane = threadIdx.x & 31;
+  MX_TILE_LOOP(A.ntc) {
+    const int c = tile * TW + lane;
+    const int64_t t = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
     double v = 0.0;
     if (c < A.nc) {
       const int4 ce = A.cedge[c];
       const int64_t o = (int64_t)l * TW;
-      double div = 0.0;
-      for (int k = 0; k < 3; ++k) {
-        const int e = cedge_k(ce, k);
-        div += csign(ce, k) * rh[tb(e, A.nz) + o] / A.emass[e];
-      }
-      if (l < A.nz - 1) div += rz[t] / mz_diag(A, t);
-      if (l > 0) div -= rz[t - TW] / mz_diag(A, t - TW);
+      double div = csign(ce, 0) * rh[tb(ce.x, A.nz) + o] * A.einv[ce.x];
+      div = fma(csign(ce, 1) * rh[tb(ce.y, A.nz) + o], A.einv[ce.y], div);
+      div = fma(csign(ce, 2) * rh[tb(ce.z, A.nz) + o], A.einv[ce.z], div);
+      if (l < A.nz - 1) div = fma(rz[t], mz_inv(A, t), div);
+      if (l > 0) div = fma(-rz[t - TW], mz_inv(A, t - TW), div);
       v = fma(-A.a * A.c2, div, rpin[t]);
     }
     rp[t] = v;
   }
 }
 
-// z_U = M2inv (r_U + a D^T z_P), z_P already in the cell part of z
-__global__ void k_mx_pre_upper(MxArgs A, const double* __restrict__ r, double* __restrict__ z) {
+// z_h = M2inv (r_h + a D_h^T z_P)
+__global__ void k_mx_pre_upper_h(MxArgs A, const double* __restrict__ r, double* __restrict__ z) {
   const double* zp = z + A.nh + A.Np;
-  const int64_t nu = A.nh + A.Np;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  MX_TILE_LOOP(A.nte) {
+    const int e = tile * TW + lane;
+    const int64_t i = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
     double v = 0.0;
-    if (i < A.nh) {
-      int e, l;
-      decode_h(i, A.nz, e, l);
-      if (e < A.ne) {
-        const int4 ed = A.edge[e];
-        const int64_t o = (int64_t)l * TW;
-        v = (r[i] + A.a * (zp[tb(ed.x, A.nz) + o] - zp[tb(ed.z, A.nz) + o])) / A.emass[e];
-      }
-    } else {
-      const int64_t t = i - A.nh;
-      int c, l;
-      decode_c(t, A.nz, c, l);
-      if (c < A.nc && l < A.nz - 1) v = (r[i] + A.a * (zp[t] - zp[t + TW])) / mz_diag(A, t);
+    if (e < A.ne) {
+      const int4 ed = A.edge[e];
+      const int64_t o = (int64_t)l * TW;
+      v = (r[i] + A.a * (zp[tb(ed.x, A.nz) + o] - zp[tb(ed.z, A.nz) + o])) * A.einv[e];
     }
     z[i] = v;
   }
 }
 
-// COLUMN <-> tiled for the whole vector: horizontal faces e * nz + l, vertical
-// faces c * (nz - 1) + l, cells c * nz + l
-__global__ void k_mx_layout(MxArgs A, bool to_tiled, const double* __restrict__ ucol, const double* __restrict__ pcol,
-                            double* __restrict__ tiled, double* __restrict__ uout, double* __restrict__ pout) {
-  const int64_t n = A.nh + 2 * A.Np;
+// z_z = M2inv (r_z + a D_z^T z_P)
+__global__ void k_mx_pre_upper_z(MxArgs A, const double* __restrict__ r, double* __restrict__ z) {
+  const double* zp = z + A.nh + A.Np;
+  const int lane = threadIdx.x & 31;
+  MX_TILE_LOOP(A.ntc) {
+    const int c = tile * TW + lane;
+    const int64_t t = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
+    double v = 0.0;
+    if (c < A.nc && l < A.nz - 1) v = (r[A.nh + t] + A.a * (zp[t] - zp[t + TW])) * mz_inv(A, t);
+    z[A.nh + t] = v;
+  }
+}
+
+// COLUMN <-> tiled: horizontal faces e * nz + l, vertical faces
+// c * (nz - 1) + l, cells c * nz + l
+__global__ void k_mx_layout_h(MxArgs A, bool to_tiled, const double* __restrict__ ucol, double* __restrict__ tiled,
+                              double* __restrict__ uout) {
+  const int lane = threadIdx.x & 31;
+  MX_TILE_LOOP(A.nte) {
+    const int e = tile * TW + lane;
+    const int64_t i = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
+    const int64_t src = (int64_t)e * A.nz + l;
+    if (to_tiled) tiled[i] = e < A.ne ? ucol[src] : 0.0;
+    else if (e < A.ne) uout[src] = tiled[i];
+  }
+}
+
+__global__ void k_mx_layout_zp(MxArgs A, bool to_tiled, const double* __restrict__ ucol,
+                               const double* __restrict__ pcol, double* __restrict__ tiled, double* __restrict__ uout,
+                               double* __restrict__ pout) {
+  const int lane = threadIdx.x & 31;
   const int64_t nhc = (int64_t)A.ne * A.nz;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t src = -1;
-    const double* from = nullptr;
-    double* to = nullptr;
-    if (i < A.nh) {
-      int e, l;
-      decode_h(i, A.nz, e, l);
-      if (e < A.ne) {
-        src = (int64_t)e * A.nz + l;
-        from = ucol;
-        to = uout;
-      }
-    } else if (i < A.nh + A.Np) {
-      int c, l;
-      decode_c(i - A.nh, A.nz, c, l);
-      if (c < A.nc && l < A.nz - 1) {
-        src = nhc + (int64_t)c * (A.nz - 1) + l;
-        from = ucol;
-        to = uout;
-      }
+  MX_TILE_LOOP(A.ntc) {
+    const int c = tile * TW + lane;
+    const int64_t t = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
+    const bool vz = c < A.nc && l < A.nz - 1, vp = c < A.nc;
+    const int64_t sz = nhc + (int64_t)c * (A.nz - 1) + l, sp = (int64_t)c * A.nz + l;
+    if (to_tiled) {
+      tiled[A.nh + t] = vz ? ucol[sz] : 0.0;
+      tiled[A.nh + A.Np + t] = vp ? pcol[sp] : 0.0;
     } else {
-      int c, l;
-      decode_c(i - A.nh - A.Np, A.nz, c, l);
-      if (c < A.nc) {
-        src = (int64_t)c * A.nz + l;
-        from = pcol;
-        to = pout;
-      }
+      if (vz) uout[sz] = tiled[A.nh + t];
+      if (vp) pout[sp] = tiled[A.nh + A.Np + t];
     }
-    if (to_tiled) tiled[i] = src >= 0 ? from[src] : 0.0;
-    else if (src >= 0) to[src] = tiled[i];
   }
 }
 
 MxArgs args_of(const Level& L, const MixedSys& M, const Phys& ph) {
-  return MxArgs{L.nc, L.nz, M.ne, L.Np, M.nh, ph.a, ph.c2, ph.wn2, M.edge, M.enb, M.ecoef, M.emass, M.cedge, M.zd, M.m3};
+  return MxArgs{L.nc, L.nz, M.ne, L.ncp / TW, M.nep / TW, L.Np, M.nh, ph.a, ph.c2, ph.wn2,
+                M.edge, M.enb, M.ecoef, M.emass, M.einv, M.cedge, M.zd, M.m3, M.zsi, 1.0 / (1.0 + ph.wn2)};
 }
 
-int grid_for(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
-}
+
+int grid_tiles(int ntiles) { return ntiles < 152 * 8 ? ntiles : 152 * 8; }
 
 }  // namespace
 
 void launch_mixed_coeffs(const Level& L, const MixedSys& M, const Phys& ph, cudaStream_t s) {
   k_mx_edge_coeffs<<<(M.nep + 127) / 128, 128, 0, s>>>(M.ne, M.nep, ph.dz, M.edge, M.cedge, L.verts, M.enb,
-                                                      M.ecoef, M.emass);
+                                                      M.ecoef, M.emass, M.einv);
   k_mx_cell_coeffs<<<(unsigned)((L.Np + 255) / 256), 256, 0, s>>>(L.nc, L.nz, L.Np, ph.R, ph.dz, L.A1, M.zd,
-                                                                   M.m3);
+                                                                   M.m3, M.zsi);
 }
 
 void launch_mixed_apply(const Level& L, const MixedSys& M, const Phys& ph, const double* x, double* y,
                         cudaStream_t s) {
-  k_mx_apply<<<grid_for(M.n), 256, 0, s>>>(args_of(L, M, ph), x, y);
+  const MxArgs A = args_of(L, M, ph);
+  k_mx_apply_h<<<grid_tiles(A.nte), MX_THREADS, 0, s>>>(A, x, y);
+  k_mx_apply_zp<<<grid_tiles(A.ntc), MX_THREADS, 0, s>>>(A, x, y);
 }
 
 void launch_mixed_pre_lower(const Level& L, const MixedSys& M, const Phys& ph, const double* r, double* rp,
                             cudaStream_t s) {
-  k_mx_pre_lower<<<grid_for(L.Np), 256, 0, s>>>(args_of(L, M, ph), r, rp);
+  const MxArgs A = args_of(L, M, ph);
+  k_mx_pre_lower<<<grid_tiles(A.ntc), MX_THREADS, 0, s>>>(A, r, rp);
 }
 
 void launch_mixed_pre_upper(const Level& L, const MixedSys& M, const Phys& ph, const double* r, double* z,
                             cudaStream_t s) {
-  k_mx_pre_upper<<<grid_for(M.nh + L.Np), 256, 0, s>>>(args_of(L, M, ph), r, z);
+  const MxArgs A = args_of(L, M, ph);
+  k_mx_pre_upper_h<<<grid_tiles(A.nte), MX_THREADS, 0, s>>>(A, r, z);
+  k_mx_pre_upper_z<<<grid_tiles(A.ntc), MX_THREADS, 0, s>>>(A, r, z);
 }
 
 void launch_mixed_layout(const Level& L, const MixedSys& M, bool to_tiled, const double* u_col, const double* p_col,
                          double* tiled, double* u_out, double* p_out, cudaStream_t s) {
-  k_mx_layout<<<grid_for(M.n), 256, 0, s>>>(MxArgs{L.nc, L.nz, M.ne, L.Np, M.nh, 0, 0, 0}, to_tiled, u_col, p_col,
-                                             tiled, u_out, p_out);
+  const MxArgs A = args_of(L, M, Phys{});
+  k_mx_layout_h<<<grid_tiles(A.nte), MX_THREADS, 0, s>>>(A, to_tiled, u_col, tiled, u_out);
+  k_mx_layout_zp<<<grid_tiles(A.ntc), MX_THREADS, 0, s>>>(A, to_tiled, u_col, p_col, tiled, u_out, p_out);
 }
 
 }  // namespace hmg

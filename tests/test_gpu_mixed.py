@@ -100,14 +100,14 @@ def test_mixed_operator_matches_oracle(r, nz, L):
         assert rel_l2(got, ref) < 1e-13
 
 
-@pytest.mark.parametrize("rtol", [1e-5, 1e-9])
-def test_mixed_solve_matches_oracle(rtol):
+@pytest.mark.parametrize("rtol,orth", [(1e-5, 1), (1e-9, 1), (1e-9, 2)])
+def test_mixed_solve_matches_oracle(rtol, orth):
     c = mcase(3, 16, 3)
     b = mixed.assembled_rhs(c.mop, gi.mixed_rhs(c.mop.nu, c.mop.M3.size))
     x_ref, info_ref = krylov.fgmres(lambda v: mixed.apply_mixed(c.mop, v),
                                     lambda v: mixed.schur_precondition(c.mop, c.ops, v), b, rtol=rtol, restart=30)
     bu, bp = c.to_gpu(b)
-    u, p, info = c.h.mixed_solve(bu, bp, rtol=rtol, restart=30)
+    u, p, info = c.h.mixed_solve(bu, bp, rtol=rtol, restart=30, orth=orth)
     assert info["converged"] == 1
     assert abs(info["iterations"] - info_ref.iterations) <= 1, (info, info_ref.iterations)
     assert info["true_rel_residual"] < 2 * rtol

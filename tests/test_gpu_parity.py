@@ -202,13 +202,13 @@ def test_solve_flexible_cg_fp64():
     assert rel_l2(c.host(x), x_ref[c.idx[0]]) <= 1e-9
 
 
-@pytest.mark.parametrize("restart", [30, 4, 1])
-def test_solve_gmres_fp64_matches_oracle(restart):
+@pytest.mark.parametrize("restart,orth", [(30, 1), (30, 2), (4, 1), (4, 2), (1, 1)])
+def test_solve_gmres_fp64_matches_oracle(restart, orth):
     c = case(3, 16, 3)
     b = gi.rhs(c.ops[0].ncells)
     x_ref, info_ref = krylov.fgmres(c.ops[0].H.dot, lambda v: multigrid.vcycle(c.ops, v), b, rtol=1e-8,
                                     restart=restart)
-    x, info = c.h.solve(c.gpu(b), krylov="gmres", restart=restart, rtol=1e-8)
+    x, info = c.h.solve(c.gpu(b), krylov="gmres", restart=restart, rtol=1e-8, orth=orth)
     assert info["converged"] == 1 and info["true_rel_residual"] < 2e-8
     assert abs(info["iterations"] - info_ref.iterations) <= 1, (info, info_ref.iterations)
     assert info["rel_residual"] == pytest.approx(info_ref.residuals[-1], rel=1e-3)
