@@ -1109,9 +1109,9 @@ hmg_status hmg_mixed_apply(hmg_ctx* ctx, const double* u, const double* p, doubl
     ensure_mixed(ctx, s);
     Level& L = ctx->lv[0];
     MixedSys& M = ctx->mx;
-    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, true, u, p, M.t1, nullptr, nullptr, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 3, launch_mixed_layout(L, M, true, u, p, M.t1, nullptr, nullptr, s));
     LAUNCHN(ctx, HMG_K_APPLY, 0, s, 2, launch_mixed_apply(L, M, ctx->ph, M.t1, M.t2, s));
-    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, false, nullptr, nullptr, M.t2, yu, yp, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 3, launch_mixed_layout(L, M, false, nullptr, nullptr, M.t2, yu, yp, s));
   });
 }
 
@@ -1130,9 +1130,9 @@ hmg_status hmg_mixed_solve(hmg_ctx* ctx, const double* bu, const double* bp, dou
     ensure_mixed(ctx, s);
     Level& L = ctx->lv[0];
     MixedSys& M = ctx->mx;
-    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, true, bu, bp, M.b, nullptr, nullptr, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 3, launch_mixed_layout(L, M, true, bu, bp, M.b, nullptr, nullptr, s));
     result = solve_mixed_tiled(ctx, *params, info, s);
-    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 2, launch_mixed_layout(L, M, false, nullptr, nullptr, M.x, u, p, s));
+    LAUNCHN(ctx, HMG_K_LAYOUT, 0, s, 3, launch_mixed_layout(L, M, false, nullptr, nullptr, M.x, u, p, s));
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
   if (st != HMG_OK) return st;

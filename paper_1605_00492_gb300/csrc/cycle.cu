@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(128)
 k_rsweep(LD<float> L, int ntiles, const TB* __restrict__ b, const float* __restrict__ u, TO* __restrict__ uo,
          const TE* __restrict__ ec, float* __restrict__ bcopy, float om1) {
   const int lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (tile >= ntiles) return;
   const int c = tile * TW + lane;
   if (c >= L.nc) return;  // padding columns stay zero
@@ -772,21 +772,22 @@ template <typename TB, typename TO, int MODE, typename TE>
 bool rsweep(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
             cudaStream_t s) {
   const int nt = ntiles_of(L);
-  const unsigned grid = (unsigned)((nt + 3) / 4);
+  const int tpb = 4;   // tiles per CTA
+  const unsigned grid = (unsigned)((nt + tpb - 1) / tpb);
   const LD<float> v = view<float>(L);
   const float om1 = (float)(1.0 - omega);
   switch (L.nz) {
     case 16:
-      k_rsweep<16, TB, TO, MODE, TE><<<grid, 128, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
-                                                         (const TE*)ec, bcopy, om1);
+      k_rsweep<16, TB, TO, MODE, TE><<<grid, 32 * tpb, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
+                                                              (const TE*)ec, bcopy, om1);
       return true;
     case 32:
-      k_rsweep<32, TB, TO, MODE, TE><<<grid, 128, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
-                                                         (const TE*)ec, bcopy, om1);
+      k_rsweep<32, TB, TO, MODE, TE><<<grid, 32 * tpb, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
+                                                              (const TE*)ec, bcopy, om1);
       return true;
     case 64:
-      k_rsweep<64, TB, TO, MODE, TE><<<grid, 128, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
-                                                         (const TE*)ec, bcopy, om1);
+      k_rsweep<64, TB, TO, MODE, TE><<<grid, 32 * tpb, 0, s>>>(v, nt, (const TB*)b, (const float*)u, (TO*)uo,
+                                                              (const TE*)ec, bcopy, om1);
       return true;
     default:
       return false;

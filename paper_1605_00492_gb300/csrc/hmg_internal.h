@@ -158,6 +158,8 @@ void launch_apply(const Level& L, int dt, const void* x, void* y, const Reduce* 
 // ---- Krylov vector kernels (krylov.cu), FP64, tiled layout of level L
 void launch_to_tiled(const Level& L, int dt, const void* col, void* tiled, cudaStream_t s);
 void launch_to_column(const Level& L, int dt, const void* tiled, void* col, cudaStream_t s);
+// tile transpose of nitems columns of nzc values (COLUMN) <-> nz tiled rows (rows >= nzc zero)
+void launch_transpose64(bool to_tiled, int nitems, int nz, int nzc, const double* src, double* dst, cudaStream_t s);
 void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,
                 const Reduce& red, cudaStream_t s);  // s0 = a.b, s1 = c.d (c may be null)
 void launch_update_p(const Level& L, double* p, const double* z, const double* sc, cudaStream_t s);

@@ -10,28 +10,36 @@ namespace hmg {
 
 namespace {
 
-__device__ __forceinline__ bool decode(int64_t t, int nz, int nc, int& c, int& l) {
-  int lane = (int)(t & 31);
-  int64_t tile = t / (TW * nz);
-  l = (int)((t >> 5) % nz);
-  c = (int)(tile * TW + lane);
-  return c < nc;
-}
-
+// COLUMN <-> TILED.  The 32 columns of a tile are one contiguous block in
+// both layouts (columns c0..c0+31 x nzc values in the COLUMN layout, rows
+// 0..nz-1 x 32 lanes in the TILED one), so each CTA transposes one tile
+// through shared memory and both sides move in whole 128/256-byte rows.
+// nzc <= nz values per column (the vertical-face vectors of the
+// velocity-pressure system have nz - 1; the tiled rows beyond nzc are zero).
 template <typename T>
-__global__ void k_to_tiled(int nc, int nz, int64_t Np, const T* __restrict__ col, T* __restrict__ tiled) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= Np) return;
-  int c, l;
-  tiled[t] = decode(t, nz, nc, c, l) ? col[(int64_t)c * nz + l] : (T)0;
-}
-
-template <typename T>
-__global__ void k_to_column(int nc, int nz, int64_t Np, const T* __restrict__ tiled, T* __restrict__ col) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= Np) return;
-  int c, l;
-  if (decode(t, nz, nc, c, l)) col[(int64_t)c * nz + l] = tiled[t];
+__global__ void k_transpose(bool to_tiled, int nitems, int nz, int nzc, int ntiles, const T* __restrict__ src,
+                            T* __restrict__ dst) {
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  T* sm = reinterpret_cast<T*>(tsm_raw);   // [nz][33]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile * TW;
+    const int64_t tb0 = (int64_t)tile * TW * nz, cb0 = (int64_t)c0 * nzc;
+    __syncthreads();
+    if (to_tiled) {
+      for (int j = warp; j < TW; j += nw)
+        for (int l = lane; l < nz; l += 32)
+          sm[l * 33 + j] = (c0 + j < nitems && l < nzc) ? src[cb0 + (int64_t)j * nzc + l] : (T)0;
+      __syncthreads();
+      for (int l = warp; l < nz; l += nw) dst[tb0 + (int64_t)l * TW + lane] = sm[l * 33 + lane];
+    } else {
+      for (int l = warp; l < nz; l += nw) sm[l * 33 + lane] = src[tb0 + (int64_t)l * TW + lane];
+      __syncthreads();
+      for (int j = warp; j < TW; j += nw)
+        if (c0 + j < nitems)
+          for (int l = lane; l < nzc; l += 32) dst[cb0 + (int64_t)j * nzc + l] = sm[l * 33 + j];
+    }
+  }
 }
 
 // The vector kernels below read and write two elements per access (16-byte
@@ -156,7 +164,6 @@ __global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __r
     b[i] = f32_to_f64(a[i]);
 }
 
-inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
 
@@ -174,18 +181,31 @@ int reduce_grid(int64_t n) {
   return (int)b;
 }
 
+template <typename T>
+void transpose(bool to_tiled, int nitems, int nz, int nzc, const void* src, void* dst, cudaStream_t s) {
+  const int ntiles = (nitems + TW - 1) / TW;
+  const int g = ntiles < 152 * 8 ? ntiles : 152 * 8;
+  const size_t smem = (size_t)nz * 33 * sizeof(T);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && configured < smem) {
+    cudaFuncSetAttribute(k_transpose<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  k_transpose<T><<<g, 256, smem, s>>>(to_tiled, nitems, nz, nzc, ntiles, (const T*)src, (T*)dst);
+}
+
 void launch_to_tiled(const Level& L, int dt, const void* col, void* tiled, cudaStream_t s) {
-  if (dt == HMG_FP64)
-    k_to_tiled<double><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const double*)col, (double*)tiled);
-  else
-    k_to_tiled<float><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const float*)col, (float*)tiled);
+  if (dt == HMG_FP64) transpose<double>(true, L.nc, L.nz, L.nz, col, tiled, s);
+  else transpose<float>(true, L.nc, L.nz, L.nz, col, tiled, s);
 }
 
 void launch_to_column(const Level& L, int dt, const void* tiled, void* col, cudaStream_t s) {
-  if (dt == HMG_FP64)
-    k_to_column<double><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const double*)tiled, (double*)col);
-  else
-    k_to_column<float><<<blocks_for(L.Np, 256), 256, 0, s>>>(L.nc, L.nz, L.Np, (const float*)tiled, (float*)col);
+  if (dt == HMG_FP64) transpose<double>(false, L.nc, L.nz, L.nz, tiled, col, s);
+  else transpose<float>(false, L.nc, L.nz, L.nz, tiled, col, s);
+}
+
+void launch_transpose64(bool to_tiled, int nitems, int nz, int nzc, const double* src, double* dst, cudaStream_t s) {
+  transpose<double>(to_tiled, nitems, nz, nzc, src, dst, s);
 }
 
 void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,

@@ -50,6 +50,12 @@ __device__ void rt0_block(const double* v, double S[3][3]) {
 }
 
 __device__ __forceinline__ int csign(const int4& ce, int k) { return ((ce.w >> k) & 1) ? -1 : 1; }
+
+// +-v by the sign bit of local edge k (an integer operation, no FP64 multiply)
+__device__ __forceinline__ double sgn_apply(const int4& ce, int k, double v) {
+  const long long neg = (long long)((ce.w >> k) & 1) << 63;
+  return __longlong_as_double(__double_as_longlong(v) ^ neg);
+}
 __device__ __forceinline__ int cedge_k(const int4& ce, int k) { return k == 0 ? ce.x : (k == 1 ? ce.y : ce.z); }
 
 // Per edge: M2^h diagonal and the four coupled edges with their entries.
@@ -114,6 +120,7 @@ struct MxArgs {
   const double* m3;
   const double* zsi;          // 1 / (zd_l + zd_(l+1))
   double inv1wn2;             // 1 / (1 + w_N^2)
+  double one_wn2, ac2;        // 1 + w_N^2, a c^2
 };
 
 // 1 / M2~ diagonal of the vertical face between layers l and l + 1 (t = its index)
@@ -165,18 +172,19 @@ __global__ void k_mx_apply_zp(MxArgs A, const double* __restrict__ x, double* __
     double vz = 0.0, vp = 0.0;
     if (c < A.nc) {
       const int64_t o = (int64_t)l * TW;
+      const double xzc = l < A.nz - 1 ? xz[t] : 0.0, xzd = l > 0 ? xz[t - TW] : 0.0;
       if (l < A.nz - 1) {
-        double m = (A.zd[t] + A.zd[t + TW]) * xz[t];
-        if (l > 0) m = fma(0.5 * A.zd[t], xz[t - TW], m);
-        if (l + 1 < A.nz - 1) m = fma(0.5 * A.zd[t + TW], xz[t + TW], m);
-        vz = fma(1.0 + A.wn2, m, -A.a * (xp[t] - xp[t + TW]));
+        // M2^z row of this face: cell l adds zd_l (x_f + x_below / 2), cell l + 1 adds zd_(l+1) (x_f + x_above / 2)
+        const double xzu = l + 1 < A.nz - 1 ? xz[t + TW] : 0.0;
+        const double m = fma(A.zd[t], fma(0.5, xzd, xzc), A.zd[t + TW] * fma(0.5, xzu, xzc));
+        vz = fma(A.one_wn2, m, -A.a * (xp[t] - xp[t + TW]));
       }
       const int4 ce = A.cedge[c];
-      double div = csign(ce, 0) * xh[tb(ce.x, A.nz) + o] + csign(ce, 1) * xh[tb(ce.y, A.nz) + o] +
-                   csign(ce, 2) * xh[tb(ce.z, A.nz) + o];
-      if (l < A.nz - 1) div += xz[t];
-      if (l > 0) div -= xz[t - TW];
-      vp = fma(A.a * A.c2, div, A.m3[t] * xp[t]);
+      double div = sgn_apply(ce, 0, xh[tb(ce.x, A.nz) + o]);
+      div += sgn_apply(ce, 1, xh[tb(ce.y, A.nz) + o]);
+      div += sgn_apply(ce, 2, xh[tb(ce.z, A.nz) + o]);
+      div += xzc - xzd;
+      vp = fma(A.ac2, div, A.m3[t] * xp[t]);
     }
     y[A.nh + t] = vz;
     y[A.nh + A.Np + t] = vp;
@@ -196,12 +204,15 @@ __global__ void k_mx_pre_lower(MxArgs A, const double* __restrict__ r, double* _
     if (c < A.nc) {
       const int4 ce = A.cedge[c];
       const int64_t o = (int64_t)l * TW;
-      double div = csign(ce, 0) * rh[tb(ce.x, A.nz) + o] * A.einv[ce.x];
-      div = fma(csign(ce, 1) * rh[tb(ce.y, A.nz) + o], A.einv[ce.y], div);
-      div = fma(csign(ce, 2) * rh[tb(ce.z, A.nz) + o], A.einv[ce.z], div);
-      if (l < A.nz - 1) div = fma(rz[t], mz_inv(A, t), div);
-      if (l > 0) div = fma(-rz[t - TW], mz_inv(A, t - TW), div);
-      v = fma(-A.a * A.c2, div, rpin[t]);
+      double div = sgn_apply(ce, 0, rh[tb(ce.x, A.nz) + o]) * A.einv[ce.x];
+      div = fma(sgn_apply(ce, 1, rh[tb(ce.y, A.nz) + o]), A.einv[ce.y], div);
+      div = fma(sgn_apply(ce, 2, rh[tb(ce.z, A.nz) + o]), A.einv[ce.z], div);
+      // vertical faces: (1 + w_N^2)^-1 applied once to their sum
+      double vz = 0.0;
+      if (l < A.nz - 1) vz = rz[t] * A.zsi[t];
+      if (l > 0) vz = fma(-rz[t - TW], A.zsi[t - TW], vz);
+      div = fma(vz, A.inv1wn2, div);
+      v = fma(-A.ac2, div, rpin[t]);
     }
     rp[t] = v;
   }
@@ -237,43 +248,10 @@ __global__ void k_mx_pre_upper_z(MxArgs A, const double* __restrict__ r, double*
   }
 }
 
-// COLUMN <-> tiled: horizontal faces e * nz + l, vertical faces
-// c * (nz - 1) + l, cells c * nz + l
-__global__ void k_mx_layout_h(MxArgs A, bool to_tiled, const double* __restrict__ ucol, double* __restrict__ tiled,
-                              double* __restrict__ uout) {
-  const int lane = threadIdx.x & 31;
-  MX_TILE_LOOP(A.nte) {
-    const int e = tile * TW + lane;
-    const int64_t i = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
-    const int64_t src = (int64_t)e * A.nz + l;
-    if (to_tiled) tiled[i] = e < A.ne ? ucol[src] : 0.0;
-    else if (e < A.ne) uout[src] = tiled[i];
-  }
-}
-
-__global__ void k_mx_layout_zp(MxArgs A, bool to_tiled, const double* __restrict__ ucol,
-                               const double* __restrict__ pcol, double* __restrict__ tiled, double* __restrict__ uout,
-                               double* __restrict__ pout) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nhc = (int64_t)A.ne * A.nz;
-  MX_TILE_LOOP(A.ntc) {
-    const int c = tile * TW + lane;
-    const int64_t t = (int64_t)tile * TW * A.nz + (int64_t)l * TW + lane;
-    const bool vz = c < A.nc && l < A.nz - 1, vp = c < A.nc;
-    const int64_t sz = nhc + (int64_t)c * (A.nz - 1) + l, sp = (int64_t)c * A.nz + l;
-    if (to_tiled) {
-      tiled[A.nh + t] = vz ? ucol[sz] : 0.0;
-      tiled[A.nh + A.Np + t] = vp ? pcol[sp] : 0.0;
-    } else {
-      if (vz) uout[sz] = tiled[A.nh + t];
-      if (vp) pout[sp] = tiled[A.nh + A.Np + t];
-    }
-  }
-}
-
 MxArgs args_of(const Level& L, const MixedSys& M, const Phys& ph) {
   return MxArgs{L.nc, L.nz, M.ne, L.ncp / TW, M.nep / TW, L.Np, M.nh, ph.a, ph.c2, ph.wn2,
-                M.edge, M.enb, M.ecoef, M.emass, M.einv, M.cedge, M.zd, M.m3, M.zsi, 1.0 / (1.0 + ph.wn2)};
+                M.edge, M.enb, M.ecoef, M.emass, M.einv, M.cedge, M.zd, M.m3, M.zsi, 1.0 / (1.0 + ph.wn2),
+                1.0 + ph.wn2, ph.a * ph.c2};
 }
 
 
@@ -310,9 +288,17 @@ void launch_mixed_pre_upper(const Level& L, const MixedSys& M, const Phys& ph, c
 
 void launch_mixed_layout(const Level& L, const MixedSys& M, bool to_tiled, const double* u_col, const double* p_col,
                          double* tiled, double* u_out, double* p_out, cudaStream_t s) {
-  const MxArgs A = args_of(L, M, Phys{});
-  k_mx_layout_h<<<grid_tiles(A.nte), MX_THREADS, 0, s>>>(A, to_tiled, u_col, tiled, u_out);
-  k_mx_layout_zp<<<grid_tiles(A.ntc), MX_THREADS, 0, s>>>(A, to_tiled, u_col, p_col, tiled, u_out, p_out);
+  // horizontal faces e * nz + l; vertical faces c * (nz - 1) + l after them; cells c * nz + l
+  const int64_t nhc = (int64_t)M.ne * L.nz;
+  if (to_tiled) {
+    launch_transpose64(true, M.ne, L.nz, L.nz, u_col, tiled, s);
+    launch_transpose64(true, L.nc, L.nz, L.nz - 1, u_col + nhc, tiled + M.nh, s);
+    launch_transpose64(true, L.nc, L.nz, L.nz, p_col, tiled + M.nh + L.Np, s);
+  } else {
+    launch_transpose64(false, M.ne, L.nz, L.nz, tiled, u_out, s);
+    launch_transpose64(false, L.nc, L.nz, L.nz - 1, tiled + M.nh, u_out + nhc, s);
+    launch_transpose64(false, L.nc, L.nz, L.nz, tiled + M.nh + L.Np, p_out, s);
+  }
 }
 
 }  // namespace hmg
