@@ -147,3 +147,37 @@ def test_r7x128_properties_both_forms():
     assert i64["true_rel_residual"] < 2e-8 and im["true_rel_residual"] < 2e-8
     assert float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)) < 1e-6
     h.close()
+
+
+def test_velocity_pressure_system_full_size():
+    """r6x64 (18.3 M unknowns): GMRES(30) with the Schur-complement
+    preconditioner converges with both V-cycle forms to the same solution; the
+    operator's off-diagonal blocks are adjoint (<D U, P> = <U, D^T P>) and its
+    velocity mass is symmetric, properties that hold at any size."""
+    h = hmg.Hierarchy(6, 64, 5)
+    h.assemble()
+    nhf, nvf, nc = h.mixed_sizes()
+    nu = nhf + nvf
+    g = torch.Generator(device=DEV).manual_seed(17)
+    U1 = torch.randn(nu, generator=g, dtype=torch.float64, device=DEV)
+    U2 = torch.randn(nu, generator=g, dtype=torch.float64, device=DEV)
+    P = torch.randn(nc, generator=g, dtype=torch.float64, device=DEV)
+    zu, zp = torch.zeros(nu, dtype=torch.float64, device=DEV), torch.zeros(nc, dtype=torch.float64, device=DEV)
+    yu_p, _ = h.mixed_apply(zu, P)            # -a D^T P
+    _, yp_u = h.mixed_apply(U1, zp)           # a c^2 D U
+    a_c2_over_minus_a = float(torch.dot(yp_u, P)) / float(torch.dot(U1, yu_p))   # = -c^2
+    assert a_c2_over_minus_a == pytest.approx(-300.0 ** 2, rel=1e-10)
+    m1, _ = h.mixed_apply(U1, zp)
+    m2, _ = h.mixed_apply(U2, zp)
+    assert float(torch.dot(m1, U2)) == pytest.approx(float(torch.dot(U1, m2)), rel=1e-12)
+    # right-hand side (M2~ R_U, M3 R_P)
+    R = torch.tensor(gi.mixed_rhs(nu, nc), dtype=torch.float64, device=DEV)
+    bu, _ = h.mixed_apply(R[:nu].contiguous(), zp)
+    _, bp = h.mixed_apply(zu, R[nu:].contiguous())
+    u64, p64, i64 = h.mixed_solve(bu, bp, rtol=1e-8)
+    um, pm, im = h.mixed_solve(bu, bp, rtol=1e-8, precision="mixed")
+    assert i64["converged"] == 1 and im["converged"] == 1
+    assert i64["true_rel_residual"] < 2e-8 and im["true_rel_residual"] < 2e-8
+    assert float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64)) < 1e-6
+    assert float(torch.linalg.norm(pm - p64) / torch.linalg.norm(p64)) < 1e-6
+    h.close()
