@@ -603,11 +603,55 @@ __device__ __forceinline__ T stencil_acc(const LD<T>& L, const T* __restrict__ x
 
 // b_c = P^T (b - H^ u): the children 4C..4C+3 of coarse column C are four
 // adjacent lanes of one tile row, so the sum over them is two shuffles.
+// Large levels (RG = 0): every resident warp takes one contiguous run of the
+// level's (tile, layer) rows, so the work is balanced to one row per warp
+// whatever the ratio of tiles to CTAs; a warp reloads the column data only
+// when its run enters a new tile.
+#define HMG_BALANCED_ROWS(NTILES, NZ, ...)                                                    \
+  {                                                                                           \
+    const int nwt = gridDim.x * NW, gw = blockIdx.x * NW + (threadIdx.x >> 5);                \
+    const int total = (NTILES) * (NZ);                                                        \
+    const int per = (total + nwt - 1) / nwt;                                                  \
+    const int r0 = gw * per, r1 = min(total, r0 + per);                                       \
+    int cur = -1;                                                                             \
+    for (int wr = r0; wr < r1; ++wr) {                                                        \
+      const int tile = wr / (NZ), l = wr - tile * (NZ);                                       \
+      const bool fresh = tile != cur;                                                         \
+      cur = tile;                                                                             \
+      __VA_ARGS__                                                                             \
+    }                                                                                         \
+  }
+
 template <typename T, typename TC, int NW>
 __global__ void __launch_bounds__(NW * 32)
 k_tresid_restrict(LD<T> L, int ntiles, int RG, const T* __restrict__ b, const T* __restrict__ u,
                   TC* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
+  if (RG == 0) {
+    const int nz = L.nz;
+    typename Vec4<T>::type g{};
+    int64_t s0 = 0, s1 = 0, s2 = 0, qc = 0, base = 0;
+    bool valid = false;
+    HMG_BALANCED_ROWS(ntiles, nz, {
+      if (fresh) {
+        const int c = tile * TW + lane;
+        valid = c < L.nc;
+        base = (int64_t)tile * TW * nz + lane;
+        const int4 nb = L.nbr[c];
+        g = L.gh[c];
+        s0 = tile_base(nb.x, nz);
+        s1 = tile_base(nb.y, nz);
+        s2 = tile_base(nb.z, nz);
+        qc = tile_base(c >> 2, nz);
+      }
+      const int64_t t = base + (int64_t)l * TW;
+      T r = stencil_acc<T, -1>(L, u, t, l, b[t], g, s0, s1, s2);
+      r += __shfl_xor_sync(0xffffffffu, r, 1);
+      r += __shfl_xor_sync(0xffffffffu, r, 2);
+      if ((lane & 3) == 0 && valid) bc[qc + (int64_t)l * TW] = cvt<TC>(r);
+    })
+    return;
+  }
   const int row0 = (blockIdx.x % RG) * NW + (threadIdx.x >> 5), rstep = RG * NW;
   const int nz = L.nz;
   for (int tile = blockIdx.x / RG; tile < ntiles; tile += gridDim.x / RG) {
@@ -641,10 +685,30 @@ template <typename T, bool DOT, int NW>
 __global__ void __launch_bounds__(NW * 32)
 k_tapply(LD<T> L, int ntiles, int RG, const T* __restrict__ x, T* __restrict__ y, Reduce red) {
   const int lane = threadIdx.x & 31;
-  const int row0 = (blockIdx.x % RG) * NW + (threadIdx.x >> 5), rstep = RG * NW;
   const int nz = L.nz;
   double acc[2] = {0.0, 0.0};  // alternate rows: no dependent FP64 chain
-  for (int tile = blockIdx.x / RG; tile < ntiles; tile += gridDim.x / RG) {
+  if (RG == 0) {
+    typename Vec4<T>::type g{};
+    int64_t s0 = 0, s1 = 0, s2 = 0, base = 0;
+    HMG_BALANCED_ROWS(ntiles, nz, {
+      if (fresh) {
+        const int c = tile * TW + lane;   // padding columns: zero stencil (see below)
+        base = (int64_t)tile * TW * nz + lane;
+        const int4 nb = L.nbr[c];
+        g = L.gh[c];
+        s0 = tile_base(nb.x, nz);
+        s1 = tile_base(nb.y, nz);
+        s2 = tile_base(nb.z, nz);
+      }
+      const int64_t t = base + (int64_t)l * TW;
+      const T v = stencil_acc<T, 1>(L, x, t, l, (T)0, g, s0, s1, s2);
+      y[t] = v;
+      if (DOT) acc[wr & 1] = fma((double)x[t], (double)v, acc[wr & 1]);
+    })
+  }
+  const int rg = RG > 0 ? RG : 1;
+  const int row0 = (blockIdx.x % rg) * NW + (threadIdx.x >> 5), rstep = rg * NW;
+  for (int tile = RG == 0 ? ntiles : blockIdx.x / rg; tile < ntiles; tile += gridDim.x / rg) {
     // padding columns (levels under 32 columns) are their own neighbours with
     // zero coefficients and data: their stencil is zero, so every lane runs
     // the same branch-free row loop and y stays zero there
@@ -686,10 +750,26 @@ struct ParCfg {
 };
 // Grid of the layer-parallel kernels: whole tiles on large levels, tiles split
 // into row groups on small ones (RG * NW <= nz).
-inline ParCfg par_cfg(const Level& L) {
+// Resident CTAs of a kernel on the whole GPU (one wave), looked up once.
+template <typename K>
+int resident_grid(K kern, int threads, int& cached) {
+  if (cached == 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    cached = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 152);
+  }
+  return cached;
+}
+
+// Large levels: FP32 kernels (memory bound) take balanced rows (RG = 0, one
+// resident wave, the launcher sizes the grid); FP64 ones (bound by the FP64
+// pipe) keep a capped grid over whole tiles, which keeps more warps resident.
+inline ParCfg par_cfg(const Level& L, bool fp32 = false) {
   const int nt = ntiles_of(L);
   const int cap = 152 * 8;
-  if (nt >= cap) return {cap, 1};
+  if (nt >= cap) return {cap, fp32 ? 0 : 1};
   int rg = 1;
   while (rg * 2 * NW_PAR <= L.nz && nt * rg * 2 <= cap) rg *= 2;
   return {nt * rg, rg};
@@ -877,38 +957,52 @@ void launch_prolong(const Level& L, int dt, void* u, const void* ec, int ec_dt, 
                                                                     (const float*)ec);
 }
 
+// grid of a layer-parallel launch: one resident wave in the balanced mode
+#define HMG_PAR_GRID(KERN, PC)                                       \
+  ([&] {                                                             \
+    static int cached_ = 0;                                          \
+    return (PC).rg == 0 ? resident_grid(KERN, NW_PAR * 32, cached_) : (PC).grid; \
+  }())
+
 void launch_resid_restrict(const Level& L, int dt, const void* b, const void* u, void* bc, int bc_dt,
                            cudaStream_t s) {
-  const ParCfg pc = par_cfg(L);
-  const int nt = ntiles_of(L), g = pc.grid, rg = pc.rg;
-  if (dt == HMG_FP64)
-    k_tresid_restrict<double, double, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<double>(L), nt, rg, (const double*)b,
-                                                                        (const double*)u, (double*)bc);
-  else if (bc_dt == HMG_FP64)
-    k_tresid_restrict<float, double, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)b,
-                                                                       (const float*)u, (double*)bc);
-  else
-    k_tresid_restrict<float, float, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)b,
-                                                                      (const float*)u, (float*)bc);
+  const ParCfg pc = par_cfg(L, dt == HMG_FP32);
+  const int nt = ntiles_of(L), rg = pc.rg;
+  if (dt == HMG_FP64) {
+    auto k = k_tresid_restrict<double, double, NW_PAR>;
+    k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<double>(L), nt, rg, (const double*)b, (const double*)u,
+                                                  (double*)bc);
+  } else if (bc_dt == HMG_FP64) {
+    auto k = k_tresid_restrict<float, double, NW_PAR>;
+    k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)b, (const float*)u,
+                                                  (double*)bc);
+  } else {
+    auto k = k_tresid_restrict<float, float, NW_PAR>;
+    k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)b, (const float*)u,
+                                                  (float*)bc);
+  }
 }
 
 void launch_apply(const Level& L, int dt, const void* x, void* y, const Reduce* red, cudaStream_t s) {
-  const ParCfg pc = par_cfg(L);
-  const int nt = ntiles_of(L), g = pc.grid, rg = pc.rg;
-  Reduce none{};
+  const ParCfg pc = par_cfg(L, dt == HMG_FP32);
+  const int nt = ntiles_of(L), rg = pc.rg;
+  const Reduce r = red ? *red : Reduce{};
   if (dt == HMG_FP64) {
-    if (red)
-      k_tapply<double, true, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<double>(L), nt, rg, (const double*)x, (double*)y,
-                                                                *red);
-    else
-      k_tapply<double, false, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<double>(L), nt, rg, (const double*)x, (double*)y,
-                                                                 none);
+    if (red) {
+      auto k = k_tapply<double, true, NW_PAR>;
+      k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<double>(L), nt, rg, (const double*)x, (double*)y, r);
+    } else {
+      auto k = k_tapply<double, false, NW_PAR>;
+      k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<double>(L), nt, rg, (const double*)x, (double*)y, r);
+    }
   } else {
-    if (red)
-      k_tapply<float, true, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)x, (float*)y, *red);
-    else
-      k_tapply<float, false, NW_PAR><<<g, NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)x, (float*)y,
-                                                                none);
+    if (red) {
+      auto k = k_tapply<float, true, NW_PAR>;
+      k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)x, (float*)y, r);
+    } else {
+      auto k = k_tapply<float, false, NW_PAR>;
+      k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)x, (float*)y, r);
+    }
   }
 }
 
