@@ -21,6 +21,9 @@ atmospheric modelling"):
                 DG0 restriction / prolongation of Sec. 3.2 and the recursive
                 correction-scheme V-cycle of Algorithm 1.
 * ``krylov``    preconditioned CG (and flexible CG) on H^ p = b.
+* ``nlo``       the next-to-lowest-order (BDFM1 x DG1 / DG1 x DG1) lumped
+                operator, its column block solve, the p-coarsening DG1 ->
+                DG0 and its V-cycle over the lowest-order hierarchy.
 * ``adjoint``   the gradient of a least-squares loss of the solution with
                 respect to the right-hand side and a per-cell coefficient of
                 the vertical coupling.
