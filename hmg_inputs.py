@@ -31,6 +31,7 @@ SEED_THETA = 2      # vertical-coupling coefficient field theta = exp(0.3 N(0,1)
 SEED_PTARGET = 3    # adjoint target p_target ~ N(0, 1)
 SEED_DIRS = 4       # finite-difference directions
 SEED_MIXED = 5      # velocity-pressure right-hand side (R_U, R_P) ~ N(0, 1)
+SEED_NLO = 6        # next-to-lowest-order right-hand side ~ N(0, 1) per unknown
 
 
 def ncolumns(refinement):
@@ -74,3 +75,9 @@ def mixed_rhs(nu, np_, seed=SEED_MIXED):
     face values, then np_ cell values, iid N(0,1) (faces in face order); the
     system's right-hand side is (M2~ R_U, M3 R_P)."""
     return normal(nu + np_, seed)
+
+
+def nlo_rhs(n, seed=SEED_NLO):
+    """Right-hand side of the next-to-lowest-order Helmholtz problem: n iid
+    N(0,1) values, one per DG1 unknown, in the oracle's unknown order."""
+    return normal(n, seed)

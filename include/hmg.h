@@ -214,6 +214,64 @@ hmg_status hmg_mixed_apply(hmg_ctx* ctx, const double* u, const double* p, doubl
 hmg_status hmg_mixed_solve(hmg_ctx* ctx, const double* bu, const double* bp, double* u, double* p,
                            const hmg_solve_params* params, hmg_solve_info* info, void* stream);
 
+/* ---- Next-to-lowest order (NLO): Table "FiniteElements" -------------------
+ * Pressure in DG1(T) x DG1(z) (6 unknowns per cell), horizontal velocity in
+ * BDFM1(T) x DG1(z), vertical velocity in DG1(T) x P2(z); H^ is Eq.
+ * (Preconditioner) for these spaces with the lumped masses of Eq.
+ * (LumpedMass), evaluated on the finest mesh of the context with the
+ * parameters of the last hmg_assemble_helmholtz (theta = 1).  Unknown order
+ * (NLO COLUMN layout): ((c * nlayers + l) * 3 + j) * 2 + m for column c,
+ * layer l, vertex j of the column's triangle (hmg_export_vertices; DG1 nodal
+ * at the vertices) and m = 0 / 1 for the bottom / top of the layer.  The
+ * BDFM1 degrees of freedom are the length-scaled normal components at the
+ * points 1/3 and 2/3 of each edge and the moments against the three Whitney
+ * functions.  The V-cycle (Sec. 4.2.1) smooths with the column block solve of
+ * Eq. (HHgeneralbanded) (block tridiagonal, 6 x 6 blocks, factorised once),
+ * p-coarsens DG1 -> DG0 on the same mesh by the natural embedding and runs
+ * the lowest-order V-cycle of the context below.  The coefficient tables
+ * (about 1.7 KB per cell) are built on the host by the first NLO call after
+ * each hmg_assemble_helmholtz. */
+
+/* Length of an NLO vector: 6 * ncols * nlayers of the finest level. */
+hmg_status hmg_nlo_size(const hmg_ctx* ctx, int64_t* n);
+
+/* verts[9 c + 3 j + x]: coordinate x of vertex j of column c's triangle on
+ * the unit sphere (the order that numbers the DG1 unknowns).  Host buffer of
+ * 9 * ncols doubles.  Errors: INVALID_ARG. */
+hmg_status hmg_export_vertices(const hmg_ctx* ctx, int level, double* verts);
+
+/* Host-only assembly of the NLO operator on the finest mesh of `mesh` (no
+ * context, no GPU): diag[36 (c nlayers + l) + 6 u + u'] = H^[(c,l,u),(c,l,u')],
+ * sub[36 (c nlayers + l) + 6 u + u'] = H^[(c,l,u),(c,l-1,u')] (zero for l = 0),
+ * nbr_blocks[36 (3 c + k) + 6 u + u'] = H^[(c,l,u),(n,l,u')] for the
+ * neighbour n = nbr[3 c + k] across the edge opposite vertex k (the same for
+ * every layer), with u = 2 j + m.  Output host buffers of 36 ncols nlayers,
+ * 36 ncols nlayers, 108 ncols doubles; nbr (3 ncols int32) and verts
+ * (9 ncols doubles) may be NULL.  Errors: INVALID_ARG. */
+hmg_status hmg_nlo_host_blocks(const hmg_mesh_params* mesh, const hmg_op_params* op, double* diag, double* sub,
+                               double* nbr_blocks, int32_t* nbr, double* verts);
+
+/* y = H^ x for NLO COLUMN-layout FP64 device vectors (x != y).
+ * Errors: INVALID_ARG, STATE (not assembled), CUDA. */
+hmg_status hmg_nlo_apply(hmg_ctx* ctx, const double* x, double* y, void* stream);
+
+/* z = V r: one NLO V-cycle from zero (NLO COLUMN layout, FP64 device
+ * vectors).  nu_pre / nu_post sweeps on the NLO level and on every
+ * lowest-order level, n_coarse on the coarsest; levels = 0 uses the NLO level
+ * and all lowest-order levels, 1 the NLO smoother alone (n_coarse sweeps),
+ * k > 1 the NLO level and k - 1 lowest-order levels.  precision MIXED runs
+ * the lowest-order levels in FP32 (the NLO level stays FP64).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+hmg_status hmg_nlo_vcycle(hmg_ctx* ctx, int precision, const double* r, double* z, int nu_pre, int nu_post,
+                          int n_coarse, int levels, void* stream);
+
+/* Solve H^ x = b (NLO COLUMN layout) with restarted flexible GMRES(restart)
+ * from x = 0, right-preconditioned by one NLO V-cycle (params as for
+ * hmg_nlo_vcycle; levels counts as there); params->krylov must be
+ * HMG_KRYLOV_GMRES.  Status and info as hmg_solve. */
+hmg_status hmg_nlo_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_params* params,
+                         hmg_solve_info* info, void* stream);
+
 /* Adjoint face contraction: grad_theta_K = -lambda^T (dH^/dtheta_K) p for the
  * theta given to the last hmg_assemble_helmholtz (all ones if NULL).  Only
  * the vertical term of Eq. (Preconditioner) depends on theta, through the two
@@ -276,7 +334,10 @@ typedef enum {
   HMG_K_ASSEMBLY = 10,
   HMG_K_THETA_GRAD = 11,
   HMG_K_ORTHO = 12,          /* GMRES: Gram-Schmidt passes, basis start, iterate update */
-  HMG_K_COUNT = 13
+  HMG_K_NLO_SWEEP = 13,      /* NLO column block relaxation */
+  HMG_K_NLO_RESID = 14,      /* NLO b_c = P^T (b - H^ u) into the lowest-order level */
+  HMG_K_NLO_APPLY = 15,      /* NLO H^ x */
+  HMG_K_COUNT = 16
 } hmg_kernel_id;
 
 typedef struct {

@@ -67,7 +67,7 @@ class KernelStat(ctypes.Structure):
 
 
 KERNELS = ["sweep0", "sweep", "prolong", "resid_restrict", "apply", "dot", "update_xr", "update_p", "layout",
-           "resid_sq", "assembly", "theta_grad", "ortho"]
+           "resid_sq", "assembly", "theta_grad", "ortho", "nlo_sweep", "nlo_resid", "nlo_apply"]
 
 
 class LevelInfo(ctypes.Structure):
@@ -94,6 +94,12 @@ _SIGNATURES = {
     "hmg_export_edges": [_P, _P],
     "hmg_mixed_apply": [_P, _P, _P, _P, _P, _P],
     "hmg_mixed_solve": [_P, _P, _P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
+    "hmg_nlo_size": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "hmg_export_vertices": [_P, _I, _P],
+    "hmg_nlo_host_blocks": [ctypes.POINTER(MeshParams), ctypes.POINTER(OpParams), _P, _P, _P, _P, _P],
+    "hmg_nlo_apply": [_P, _P, _P, _P],
+    "hmg_nlo_vcycle": [_P, _I, _P, _P, _I, _I, _I, _I, _P],
+    "hmg_nlo_solve": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
     "hmg_to_layout": [_P, _I, _I, _P, _I, _P, _P],
     "hmg_sync": [_P, _P],
     "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
@@ -300,6 +306,50 @@ class Hierarchy:
             self._check(st)
         return u, p, d
 
+    # ---- next-to-lowest order (Table "FiniteElements": DG1 pressure, BDFM1 x DG1 velocity)
+
+    def nlo_size(self):
+        """Length of an NLO vector: 6 unknowns per cell of the finest level."""
+        n = ctypes.c_int64()
+        self._check(self.lib.hmg_nlo_size(self._ctx, ctypes.byref(n)))
+        return n.value
+
+    def export_vertices(self, level=0):
+        """(ncols, 3, 3) unit-sphere vertices of each column's triangle, in
+        the order that numbers the NLO unknowns."""
+        import numpy as np
+        v = np.zeros((self.levels[level]["ncols"], 3, 3))
+        self._check(self.lib.hmg_export_vertices(self._ctx, level, v.ctypes.data_as(_P)))
+        return v
+
+    def nlo_apply(self, x, out=None, stream=None):
+        """y = H^ x for the NLO operator (COLUMN layout, FP64 device tensors)."""
+        y = out if out is not None else torch.empty_like(x)
+        self._check(self.lib.hmg_nlo_apply(self._ctx, _ptr(x.contiguous()), _ptr(y), _stream(stream)))
+        return y
+
+    def nlo_vcycle(self, r, precision="fp64", nu_pre=2, nu_post=2, n_coarse=2, levels=0, out=None, stream=None):
+        """z = V r: one NLO V-cycle (p-coarsening to the lowest-order hierarchy)."""
+        z = out if out is not None else torch.empty_like(r)
+        self._check(self.lib.hmg_nlo_vcycle(self._ctx, PRECISION[precision], _ptr(r.contiguous()), _ptr(z), nu_pre,
+                                            nu_post, n_coarse, levels, _stream(stream)))
+        return z
+
+    def nlo_solve(self, b, out=None, stream=None, raise_on_failure=True, **kw):
+        """x = H^^-1 b for the NLO operator by GMRES(restart) with the NLO
+        V-cycle; keyword arguments as solve.  Returns (x, info dict)."""
+        kw.setdefault("krylov", "gmres")
+        x = out if out is not None else torch.empty_like(b)
+        info = SolveInfo()
+        prm = self.solve_params(**kw)
+        st = self.lib.hmg_nlo_solve(self._ctx, _ptr(b.contiguous()), _ptr(x), ctypes.byref(prm), ctypes.byref(info),
+                                    _stream(stream))
+        d = info.as_dict()
+        d["status"] = STATUS.get(st, st)
+        if raise_on_failure:
+            self._check(st)
+        return x, d
+
     def theta_grad(self, p, lam, out=None, stream=None):
         g = out if out is not None else torch.empty_like(p)
         self._check(self.lib.hmg_theta_grad(self._ctx, _ptr(p.contiguous()), _ptr(lam.contiguous()), _ptr(g),
@@ -335,6 +385,25 @@ class Hierarchy:
 
     def sync(self, stream=None):
         self._check(self.lib.hmg_sync(self._ctx, _stream(stream)))
+
+
+def nlo_host_blocks(refinement, nlayers, c=300.0, N=0.01, nu_cfl=8.0, dx_m=0.0, omega=0.8, radius_m=6.371e6,
+                    thickness_m=1.0e4):
+    """Host-only assembly of the NLO operator's blocks on the finest mesh
+    (no GPU): returns dict(diag (ncols, nlayers, 6, 6), sub (same), nbr_blocks
+    (ncols, 3, 6, 6), nbr (ncols, 3), verts (ncols, 3, 3))."""
+    import numpy as np
+    lib = load_library()
+    nc = 20 * 4 ** refinement
+    mp = MeshParams(refinement, nlayers, 1, radius_m, thickness_m)
+    op = OpParams(c, N, nu_cfl, dx_m, omega)
+    out = dict(diag=np.zeros((nc, nlayers, 6, 6)), sub=np.zeros((nc, nlayers, 6, 6)),
+               nbr_blocks=np.zeros((nc, 3, 6, 6)), nbr=np.zeros((nc, 3), dtype=np.int32), verts=np.zeros((nc, 3, 3)))
+    st = lib.hmg_nlo_host_blocks(ctypes.byref(mp), ctypes.byref(op), *(out[k].ctypes.data_as(_P) for k in
+                                                                        ("diag", "sub", "nbr_blocks", "nbr", "verts")))
+    if st != 0:
+        raise HMGError(st, lib.hmg_last_error(None).decode())
+    return out
 
 
 def convert(x, dtype, stream=None):

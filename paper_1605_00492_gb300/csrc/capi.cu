@@ -782,6 +782,134 @@ hmg_status solve_mixed_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_in
   return gmres_run(c, sys, p, info, s);
 }
 
+// ------------------------------------------------------------ next-to-lowest order
+
+Phys make_phys(const hmg_mesh_params& mp, const hmg_op_params& p) {
+  const double dx = p.dx_m > 0 ? p.dx_m : 90.0e3 * std::ldexp(1.0, 6 - mp.refinement);
+  const double dt = p.nu_cfl * dx / p.c;
+  const double wc = 0.5 * p.c * dt, wn = 0.5 * p.N * dt;
+  Phys ph;
+  ph.R = mp.radius_m;
+  ph.dz = mp.thickness_m / mp.nlayers;
+  ph.wc2 = wc * wc;
+  ph.vfac = wc * wc / (1.0 + wn * wn);
+  ph.omega = p.omega;
+  ph.a = 0.5 * dt;
+  ph.c2 = p.c * p.c;
+  ph.wn2 = wn * wn;
+  return ph;
+}
+
+void check_op_params(const hmg_op_params* p) {
+  require(p != nullptr, "params is NULL");
+  require(p->c > 0 && std::isfinite(p->c), "c must be positive");
+  require(p->N >= 0 && std::isfinite(p->N), "N must be >= 0");
+  require(p->nu_cfl > 0 && std::isfinite(p->nu_cfl), "nu_cfl must be positive");
+  require(p->omega > 0 && p->omega < 2, "omega must be in (0, 2)");
+}
+
+// Coefficient tables of the NLO level for the current assembly (host
+// assembly and factorisation, one upload).
+void ensure_nlo(hmg_ctx* c) {
+  NloSys& X = c->nlo;
+  if (X.ready) return;
+  const Level& L = c->lv[0];
+  require(L.nc % NLO_TILE == 0, "NLO needs a multiple of 5 columns");
+  if (!X.allocated) {
+    X.nt = L.nc / NLO_TILE;
+    X.n = (int64_t)X.nt * L.nz * 32;
+    const size_t cw = (size_t)X.n * 6;
+    X.Ad = dalloc<double>(c, cw);
+    X.Cs = dalloc<double>(c, cw);
+    X.Cu = dalloc<double>(c, cw);
+    X.Lf = dalloc<double>(c, cw);
+    X.Di = dalloc<double>(c, cw);
+    X.Lb = dalloc<double>(c, cw);
+    X.Nb = dalloc<double>(c, (size_t)X.nt * 3 * 6 * 32);
+    X.nb = dalloc<int>(c, (size_t)X.nt * 3 * 32);
+    for (double** v : {&X.b, &X.x, &X.t1, &X.t2, &X.w, &X.ua, &X.ub}) *v = dalloc<double>(c, X.n);
+    X.allocated = true;
+  }
+  const NloHost H = nlo_assemble_host(L.verts_host, L.nbr_host, L.nc, L.nz, c->ph);
+  std::vector<double> Lf, Dinv;
+  nlo_factor_host(H, c->ph.omega, Lf, Dinv);
+  std::vector<double> Ad, Cs, Cu, Lft, Dit, Lb, Nb;
+  std::vector<int> nb;
+  nlo_pack_host(H, Lf, Dinv, L.nbr_host, &Ad, &Cs, &Cu, &Lft, &Dit, &Lb, &Nb, &nb);
+  auto up = [](void* dst, const void* src, size_t bytes) {
+    cuda_ok(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "NLO upload");
+  };
+  up(X.Ad, Ad.data(), Ad.size() * sizeof(double));
+  up(X.Cs, Cs.data(), Cs.size() * sizeof(double));
+  up(X.Cu, Cu.data(), Cu.size() * sizeof(double));
+  up(X.Lf, Lft.data(), Lft.size() * sizeof(double));
+  up(X.Di, Dit.data(), Dit.size() * sizeof(double));
+  up(X.Lb, Lb.data(), Lb.size() * sizeof(double));
+  up(X.Nb, Nb.data(), Nb.size() * sizeof(double));
+  up(X.nb, nb.data(), nb.size() * sizeof(int));
+  X.ready = true;
+}
+
+// The lowest-order cycle configuration below the NLO level: levels = 0 all,
+// 1 none (the NLO smoother alone), k > 1 the first k - 1.
+CycleCfg nlo_cfg(const hmg_ctx* c, int nu_pre, int nu_post, int n_coarse, int levels, int precision) {
+  CycleCfg cfg = make_cfg(c, nu_pre, nu_post, n_coarse, levels > 1 ? levels - 1 : 0, precision);
+  if (levels == 1) cfg.nlev = 0;
+  return cfg;
+}
+
+// out <- V b on the NLO level (tiled NLO vectors, zero initial guess); out
+// must not be nlo.ua or nlo.ub.
+void nlo_cycle(hmg_ctx* c, const CycleCfg& cfg, const double* b, double* out, cudaStream_t s) {
+  NloSys& X = c->nlo;
+  Level& L0 = c->lv[0];
+  const int nz = L0.nz;
+  const bool single = cfg.nlev == 0;
+  const int npre = single ? cfg.n_coarse : cfg.nu_pre;
+  if (single && npre == 1) {
+    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, nullptr, out, cfg.omega, s));
+    return;
+  }
+  LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, nullptr, X.ua, cfg.omega, s));
+  double* cur = X.ua;
+  double* nxt = X.ub;
+  for (int i = 1; i < npre; ++i) {
+    const bool last = single && i == npre - 1;
+    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, cur, last ? out : nxt, cfg.omega, s));
+    if (last) return;
+    std::swap(cur, nxt);
+  }
+  if (L0.ncp > L0.nc) cuda_ok(cudaMemsetAsync(L0.b64, 0, (size_t)L0.Np * sizeof(double), s), "memset");
+  LAUNCH(c, HMG_K_NLO_RESID, 0, s, launch_nlo_resid_restrict(X, L0, b, cur, L0.b64, s));
+  cycle(c, cfg, 0, L0.b64, HMG_FP64, L0.ux64, HMG_FP64, s);
+  LAUNCH(c, HMG_K_PROLONG, 0, s, launch_nlo_prolong(X, L0, cur, L0.ux64, s));
+  for (int i = 0; i < cfg.nu_post; ++i) {
+    const bool last = i == cfg.nu_post - 1;
+    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, cur, last ? out : nxt, cfg.omega, s));
+    std::swap(cur, nxt);
+  }
+}
+
+// GMRES(m) on the NLO system (tiled nlo.b, nlo.x), right-preconditioned by
+// one NLO V-cycle.
+hmg_status solve_nlo_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  NloSys& X = c->nlo;
+  const int nz = c->lv[0].nz;
+  const CycleCfg cfg = nlo_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
+  KrylovSystem sys;
+  sys.n = X.n;
+  sys.b = X.b;
+  sys.x = X.x;
+  sys.tmp = X.t1;
+  sys.apply = [c, &X, nz](const double* x, double* y, cudaStream_t st) {
+    LAUNCH(c, HMG_K_NLO_APPLY, 0, st, launch_nlo_apply(X, nz, x, y, st));
+  };
+  sys.precond = [c, cfg](const double* r, double* z, cudaStream_t st) { nlo_cycle(c, cfg, r, z, st); };
+  sys.orth = p.orth == 2 ? 2 : 1;
+  sys.key = (3LL << 60) + (sys.orth == 2 ? (1LL << 59) : 0) + graph_key(cfg, true, 0);
+  return gmres_run(c, sys, p, info, s);
+}
+
 void check_solve_params(const hmg_solve_params* p) {
   require(p != nullptr, "params is NULL");
   require(p->precision == HMG_PRECISION_FP64 || p->precision == HMG_PRECISION_MIXED, "bad precision");
@@ -854,6 +982,7 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
       L.twist = (L.ncp / TW <= SMALL_LEVEL_TILES) ? L.nz / 2 : L.nz - 1;
       L.centroid_host = H.centroid;
       L.nbr_host = H.nbr;
+      L.verts_host = H.verts;
       std::vector<int4> nb(L.ncp);
       for (int col = 0; col < L.ncp; ++col) {
         if (col < L.nc) nb[col] = make_int4(H.nbr[3 * col], H.nbr[3 * col + 1], H.nbr[3 * col + 2], 0);
@@ -950,26 +1079,12 @@ hmg_status hmg_export_mesh(const hmg_ctx* ctx, int level, double* centroids, int
 hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const double* theta, void* stream) {
   if (!ctx) return HMG_ERR_INVALID_ARG;
   return guarded(ctx, [&] {
-    require(p != nullptr, "params is NULL");
-    require(p->c > 0 && std::isfinite(p->c), "c must be positive");
-    require(p->N >= 0 && std::isfinite(p->N), "N must be >= 0");
-    require(p->nu_cfl > 0 && std::isfinite(p->nu_cfl), "nu_cfl must be positive");
-    require(p->omega > 0 && p->omega < 2, "omega must be in (0, 2)");
+    check_op_params(p);
     cudaStream_t s = as_stream(stream);
     ctx->assembled = false;
+    ctx->nlo.ready = false;
     ctx->op = *p;
-    double dx = p->dx_m > 0 ? p->dx_m : 90.0e3 * std::ldexp(1.0, 6 - ctx->mp.refinement);
-    double dt = p->nu_cfl * dx / p->c;
-    double wc = 0.5 * p->c * dt, wn = 0.5 * p->N * dt;
-    Phys& ph = ctx->ph;
-    ph.R = ctx->mp.radius_m;
-    ph.dz = ctx->mp.thickness_m / ctx->mp.nlayers;
-    ph.wc2 = wc * wc;
-    ph.vfac = wc * wc / (1.0 + wn * wn);
-    ph.omega = p->omega;
-    ph.a = 0.5 * dt;
-    ph.c2 = p->c * p->c;
-    ph.wn2 = wn * wn;
+    const Phys& ph = (ctx->ph = make_phys(ctx->mp, *p));
     ctx->has_theta = theta != nullptr;
     if (theta) {
       LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(ctx->lv[0], HMG_FP64, theta, ctx->lv[0].theta, s));
@@ -1142,6 +1257,101 @@ hmg_status hmg_mixed_solve(hmg_ctx* ctx, const double* bu, const double* bp, dou
   return result;
 }
 
+hmg_status hmg_nlo_size(const hmg_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return HMG_ERR_INVALID_ARG;
+  *n = 6 * ctx->lv[0].N;
+  return HMG_OK;
+}
+
+hmg_status hmg_export_vertices(const hmg_ctx* ctx, int level, double* verts) {
+  if (!ctx || !verts || level < 0 || level >= (int)ctx->lv.size()) return HMG_ERR_INVALID_ARG;
+  const Level& L = ctx->lv[level];
+  std::memcpy(verts, L.verts_host.data(), L.verts_host.size() * sizeof(double));
+  return HMG_OK;
+}
+
+hmg_status hmg_nlo_host_blocks(const hmg_mesh_params* mesh, const hmg_op_params* op, double* diag, double* sub,
+                               double* nbr_blocks, int32_t* nbr, double* verts) {
+  hmg_status st = guarded(nullptr, [&] {
+    require(mesh != nullptr, "mesh is NULL");
+    require(mesh->refinement >= 0 && mesh->refinement <= 8, "refinement must be in [0, 8]");
+    require(mesh->nlayers >= 1 && mesh->nlayers <= 256, "nlayers must be in [1, 256]");
+    require(mesh->radius_m > 0 && mesh->thickness_m > 0, "radius_m and thickness_m must be positive");
+    check_op_params(op);
+    require(diag && sub && nbr_blocks, "diag, sub and nbr_blocks must be non-NULL host buffers");
+    std::vector<HostLevel> host = build_mesh_hierarchy(mesh->refinement, 1);
+    const HostLevel& H = host[0];
+    const NloHost B = nlo_assemble_host(H.verts, H.nbr, H.ncols, mesh->nlayers, make_phys(*mesh, *op));
+    std::memcpy(diag, B.diag.data(), B.diag.size() * sizeof(double));
+    std::memcpy(sub, B.sub.data(), B.sub.size() * sizeof(double));
+    std::memcpy(nbr_blocks, B.nbr.data(), B.nbr.size() * sizeof(double));
+    if (nbr) std::memcpy(nbr, H.nbr.data(), H.nbr.size() * sizeof(int32_t));
+    if (verts) std::memcpy(verts, H.verts.data(), H.verts.size() * sizeof(double));
+  });
+  return st;
+}
+
+hmg_status hmg_nlo_apply(hmg_ctx* ctx, const double* x, double* y, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(x && y && x != y, "x and y must be distinct non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_nlo(ctx);
+    NloSys& X = ctx->nlo;
+    const int nz = ctx->lv[0].nz;
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, true, x, X.t1, s));
+    LAUNCH(ctx, HMG_K_NLO_APPLY, 0, s, launch_nlo_apply(X, nz, X.t1, X.t2, s));
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, false, X.t2, y, s));
+  });
+}
+
+hmg_status hmg_nlo_vcycle(hmg_ctx* ctx, int precision, const double* r, double* z, int nu_pre, int nu_post,
+                          int n_coarse, int levels, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(precision == HMG_PRECISION_FP64 || precision == HMG_PRECISION_MIXED, "bad precision");
+    require(r && z && r != z, "r and z must be distinct non-NULL device pointers");
+    check_cycle_params(nu_pre, nu_post, n_coarse);
+    require(levels >= 0 && levels <= (int)ctx->lv.size() + 1, "levels must be in [0, nlevels + 1]");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_nlo(ctx);
+    NloSys& X = ctx->nlo;
+    const int nz = ctx->lv[0].nz;
+    const CycleCfg cfg = nlo_cfg(ctx, nu_pre, nu_post, n_coarse, levels, precision);
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, true, r, X.t1, s));
+    nlo_cycle(ctx, cfg, X.t1, X.t2, s);
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, false, X.t2, z, s));
+  });
+}
+
+hmg_status hmg_nlo_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_params* params,
+                         hmg_solve_info* info, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  hmg_status result = HMG_OK;
+  hmg_status st = guarded(ctx, [&] {
+    check_solve_params(params);
+    require(params->krylov == HMG_KRYLOV_GMRES, "the NLO solve runs GMRES (krylov = HMG_KRYLOV_GMRES)");
+    require(params->levels <= (int)ctx->lv.size() + 1, "levels must be in [0, nlevels + 1]");
+    require(b && x, "b and x must be non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_nlo(ctx);
+    NloSys& X = ctx->nlo;
+    const int nz = ctx->lv[0].nz;
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, true, b, X.b, s));
+    result = solve_nlo_tiled(ctx, *params, info, s);
+    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, false, X.x, x, s));
+    cuda_ok(cudaStreamSynchronize(s), "solve");
+  });
+  if (st != HMG_OK) return st;
+  if (result == HMG_ERR_NOT_CONVERGED) ctx->err = "maximum number of iterations reached";
+  if (result == HMG_ERR_BREAKDOWN) ctx->err = "GMRES breakdown";
+  if (result == HMG_ERR_NONFINITE) ctx->err = "non-finite residual";
+  return result;
+}
+
 hmg_status hmg_theta_grad(hmg_ctx* ctx, const double* p, const double* lambda, double* grad, void* stream) {
   if (!ctx) return HMG_ERR_INVALID_ARG;
   return guarded(ctx, [&] {
@@ -1175,7 +1385,8 @@ hmg_status hmg_to_layout(hmg_ctx* ctx, int level, int src_layout, const double* 
 const char* hmg_kernel_name(int kernel) {
   static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",     "prolong",  "resid_restrict", "apply",
                                            "dot",    "update_xr", "update_p", "layout",         "resid_sq",
-                                           "assembly", "theta_grad", "ortho"};
+                                           "assembly", "theta_grad", "ortho",    "nlo_sweep",      "nlo_resid",
+                                           "nlo_apply"};
   return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
 }
 

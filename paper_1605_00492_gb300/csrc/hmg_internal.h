@@ -50,6 +50,7 @@ struct Level {
   int64_t N = 0, Np = 0;
   std::vector<double> centroid_host;
   std::vector<int32_t> nbr_host;
+  std::vector<double> verts_host;   // nc * 9
   // geometry
   int4* nbr = nullptr;
   double* verts = nullptr;    // ncp * 9
@@ -127,6 +128,55 @@ void launch_mixed_pre_upper(const Level& L, const MixedSys& M, const Phys& ph, c
                             cudaStream_t s);  // z_U = M2inv (r_U + a D^T z_P)
 void launch_mixed_layout(const Level& L, const MixedSys& M, bool to_tiled, const double* u_col, const double* p_col,
                          double* tiled, double* u_out, double* p_out, cudaStream_t s);
+
+// ---- next-to-lowest order (nlo_setup.cpp: host assembly; nlo.cu: kernels)
+// Column blocks of the NLO operator per cell (6 x 6, row-major, unknown
+// u = 2 j + m): diag = H^[(c,l),(c,l)], sub = H^[(c,l),(c,l-1)]; nbr =
+// H^[(c,l),(n_k,l)] per column and local edge k (layer independent).
+struct NloHost {
+  int nc = 0, nz = 0;
+  std::vector<double> diag, sub, nbr;
+};
+NloHost nlo_assemble_host(const std::vector<double>& verts, const std::vector<int32_t>& nbr, int nc, int nz,
+                          const Phys& ph);
+// Block L D L^T of the column part: Lf[cell] = L_l (zero at l = 0),
+// Dinv[cell] = omega Dt_l^-1.
+void nlo_factor_host(const NloHost& H, double omega, std::vector<double>& Lf, std::vector<double>& Dinv);
+
+constexpr int NLO_TILE = 5;   // columns per warp: lanes 6 c5 + u, lanes 30 and 31 padding
+// The NLO system of the finest mesh.  Vectors: tiles of 5 columns, one row
+// of 32 doubles per (tile, layer), index (t * nz + l) * 32 + 6 c5 + u
+// (columns 5 t + c5); padding lanes zero.  Coefficients: 6 rows of 32 per
+// (tile, layer), index ((t * nz + l) * 6 + e) * 32 + lane = entry (u, e) of
+// the lane's cell: Ad the diagonal block, Cs the sub-diagonal block, Cu the
+// super-diagonal block (C_(l+1)^T), Lf the forward multipliers L_l, Di
+// omega Dt_l^-1, Lb the backward multipliers L_(l+1)^T.  Nb: 6 rows of 32 per
+// (tile, edge k); nb: per (tile, edge k, lane) the offset of the neighbour
+// column's row 0 plus its 6 c5.
+struct NloSys {
+  bool ready = false;        // coefficients of the current assembly uploaded
+  bool allocated = false;
+  int nt = 0;
+  int64_t n = 0;             // nt * nz * 32
+  double *Ad = nullptr, *Cs = nullptr, *Cu = nullptr, *Lf = nullptr, *Di = nullptr, *Lb = nullptr;
+  double* Nb = nullptr;
+  int* nb = nullptr;
+  double *b = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr, *w = nullptr, *ua = nullptr, *ub = nullptr;
+};
+void nlo_pack_host(const NloHost& H, const std::vector<double>& Lf, const std::vector<double>& Dinv,
+                   const std::vector<int32_t>& nbr, std::vector<double>* Ad, std::vector<double>* Cs,
+                   std::vector<double>* Cu, std::vector<double>* Lft, std::vector<double>* Dit,
+                   std::vector<double>* Lb, std::vector<double>* Nb, std::vector<int>* nb);
+void launch_nlo_layout(const NloSys& X, int nz, bool to_tiled, const double* src, double* dst, cudaStream_t s);
+void launch_nlo_apply(const NloSys& X, int nz, const double* x, double* y, cudaStream_t s);
+// bc (lowest-order level L0, TILED) = P^T (b - H^ u), P the embedding DG0 -> DG1
+void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, const double* b, const double* u, double* bc,
+                               cudaStream_t s);
+// uo = u + omega H^_z^-1 (b - H^ u); u == nullptr: from u = 0
+void launch_nlo_sweep(const NloSys& X, int nz, const double* b, const double* u, double* uo, double omega,
+                      cudaStream_t s);
+// u += P ec, ec on the lowest-order level L0 (TILED)
+void launch_nlo_prolong(const NloSys& X, const Level& L0, double* u, const double* ec, cudaStream_t s);
 
 // ---- assembly (assemble.cu)
 void launch_geometry(const Level& L, cudaStream_t s);
@@ -258,4 +308,5 @@ struct hmg_ctx {
   double* gm_host = nullptr;      // page-locked copy of gm_small
 
   hmg::MixedSys mx;               // velocity-pressure system, set up by its first use
+  hmg::NloSys nlo;                // next-to-lowest-order system, set up by its first use
 };
