@@ -38,9 +38,14 @@ WORKLOAD = "r6x64"
 def workload_desc(name):
     import hmg_inputs as gi
     w = gi.WORKLOADS[name]
-    return (f"icosahedral refinement {w['refinement']} ({gi.ncolumns(w['refinement'])} columns) x "
-            f"{w['nlayers']} layers, R = 6371 km, H = 10 km, {w['nlevels']} levels, nu_CFL = 8, omega = 0.8, "
-            "2 pre / 2 post sweeps, 2 coarsest sweeps, PCG to 1e-8")
+    shell = (f"icosahedral refinement {w['refinement']} ({gi.ncolumns(w['refinement'])} columns) x "
+             f"{w['nlayers']} layers, R = 6371 km, H = 10 km, ")
+    if w.get("order") == "nlo":
+        return shell + (f"next-to-lowest order (DG1 pressure, 6 unknowns per cell), the NLO level plus "
+                        f"{w['nlevels']} lowest-order levels, nu_CFL = 8, omega = 0.8, 2 pre / 2 post sweeps, "
+                        "2 coarsest sweeps, GMRES(30) to 1e-5")
+    return shell + (f"{w['nlevels']} levels, nu_CFL = 8, omega = 0.8, "
+                    "2 pre / 2 post sweeps, 2 coarsest sweeps, PCG to 1e-8")
 # PCG iterations of the full FP64 solve of this workload (oracle and GPU agree;
 # asserted by tests/test_gpu_fullsize.py).  Used to scale the oracle sample.
 ORACLE_ITERATIONS = 11
@@ -275,6 +280,64 @@ def cpu_baseline_subprocess(workload, iterations):
 
 # ---------------------------------------------------------------- GPU arm
 
+# NLO column-block sweep, per cell: three 6 x 6 blocks of coefficients (L_l,
+# omega Dt_l^-1, L_(l+1)^T), b, u, u' and the forward results written and read
+# back (6 unknowns each); three neighbour blocks, the forward and backward
+# block products and the relaxation: 6 x (18 + 6 + 12 + 1) FMA.
+NLO_SWEEP_BYTES_PER_CELL = 3 * 36 * 8 + 5 * 6 * 8
+NLO_SWEEP_FLOPS_PER_CELL = 2 * 6 * (18 + 6 + 12 + 1)
+
+
+def nlo_section(args, world, dev, stream, hbm):
+    import torch
+
+    import hmg_inputs as gi
+    import paper_1605_00492_gb300 as hmg
+    w = gi.WORKLOADS["r4x64nlo"]
+    h = hmg.Hierarchy(w["refinement"], w["nlayers"], w["nlevels"])
+    h.assemble()
+    n = h.nlo_size()
+    ncells = n // 6
+    b = torch.tensor(gi.nlo_rhs(n), dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "r4x64nlo: " + workload_desc("r4x64nlo"), "unknowns_pressure": n, "rtol": 1e-5,
+           "krylov": "GMRES(30), one NLO V-cycle (column block relaxation, p-coarsening DG1 -> DG0, "
+                     "4 lowest-order levels)"}
+    for form in ("fp64", "mixed"):
+        kw = dict(precision=form, rtol=1e-5, restart=30, max_iter=300)
+        for _ in range(2):
+            h.nlo_solve(b, out=x, **kw)
+        reps = max(5, min(args.steps, 20))
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            _, info = h.nlo_solve(b, out=x, **kw)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / reps
+        out[form] = {"solves_per_s": round(world / (ms / 1e3), 3), "ms_per_solve": round(ms, 4),
+                     "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"]}
+    # the NLO sweep, traced inside FP64 solves
+    h.profile_start(kernels=["nlo_sweep"], levels=[0])
+    for _ in range(3):
+        h.nlo_solve(b, out=x, precision="fp64", rtol=1e-5, restart=30, max_iter=300)
+    rec = h.profile_stop()
+    cnt, tot = rec.get(("nlo_sweep", 0), (0, 0.0))
+    avg_ms = tot / max(cnt, 1)
+    tflops = NLO_SWEEP_FLOPS_PER_CELL * ncells / (avg_ms * 1e-3) / 1e12
+    gbs = NLO_SWEEP_BYTES_PER_CELL * ncells / (avg_ms * 1e-3) / 1e9
+    out["sweep_roofline"] = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                             "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                             "hbm_achieved_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                             "kernel": "nlo_sweep (general sweep, 3 of the 4 per V-cycle)",
+                             "launches": cnt, "avg_us": round(avg_ms * 1e3, 2),
+                             "bytes_per_launch": NLO_SWEEP_BYTES_PER_CELL * ncells,
+                             "flops_per_launch": NLO_SWEEP_FLOPS_PER_CELL * ncells}
+    h.close()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -389,6 +452,10 @@ def run_gpu(args):
         vp[form] = {"solves_per_s": round(world / (ms / 1e3), 3), "ms_per_solve": round(ms, 4),
                     "iterations": infovp["iterations"], "true_rel_residual": infovp["true_rel_residual"]}
 
+    # ---- next-to-lowest order (Table "GridSetup": 5,120 columns x 64 layers,
+    # 5 levels counting the p-coarsened one), GMRES(30) to the paper's 1e-5
+    nlo = nlo_section(args, world, dev, stream, hbm) if not args.no_nlo else None
+
     # ---- end to end: host buffers through the C ABI (H2D + solve + D2H)
     e2e = None
     if not args.no_e2e:
@@ -444,6 +511,7 @@ def run_gpu(args):
                   "krylov": "flexible CG", "dtype": "f32 cycle / f64 Krylov + coarsest"},
         "vcycle": vc,
         "velocity_pressure": vp,
+        "nlo": nlo,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -596,6 +664,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-nlo", action="store_true", help="skip the next-to-lowest-order section")
     ap.add_argument("--oracle-iterations", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")

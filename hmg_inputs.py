@@ -22,6 +22,9 @@ WORKLOADS = {
     "r6x64m": dict(refinement=6, nlayers=64, nlevels=5, precision="mixed"),
     "r5x64a": dict(refinement=5, nlayers=64, nlevels=5, precision="fp64", theta=True),
     "r7x128": dict(refinement=7, nlayers=128, nlevels=6, precision="both"),
+    # next-to-lowest order (Table "GridSetup"): 5,120 columns x 64 layers, the
+    # NLO level plus 4 lowest-order levels (refinements 4 .. 1)
+    "r4x64nlo": dict(refinement=4, nlayers=64, nlevels=4, precision="both", order="nlo"),
 }
 
 # One seed per independent draw.

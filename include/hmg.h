@@ -334,10 +334,11 @@ typedef enum {
   HMG_K_ASSEMBLY = 10,
   HMG_K_THETA_GRAD = 11,
   HMG_K_ORTHO = 12,          /* GMRES: Gram-Schmidt passes, basis start, iterate update */
-  HMG_K_NLO_SWEEP = 13,      /* NLO column block relaxation */
+  HMG_K_NLO_SWEEP = 13,      /* NLO column block relaxation (after the first) */
   HMG_K_NLO_RESID = 14,      /* NLO b_c = P^T (b - H^ u) into the lowest-order level */
   HMG_K_NLO_APPLY = 15,      /* NLO H^ x */
-  HMG_K_COUNT = 16
+  HMG_K_NLO_SWEEP0 = 16,     /* NLO first column block relaxation from u = 0 */
+  HMG_K_COUNT = 17
 } hmg_kernel_id;
 
 typedef struct {

@@ -67,7 +67,8 @@ class KernelStat(ctypes.Structure):
 
 
 KERNELS = ["sweep0", "sweep", "prolong", "resid_restrict", "apply", "dot", "update_xr", "update_p", "layout",
-           "resid_sq", "assembly", "theta_grad", "ortho", "nlo_sweep", "nlo_resid", "nlo_apply"]
+           "resid_sq", "assembly", "theta_grad", "ortho", "nlo_sweep", "nlo_resid", "nlo_apply",
+           "nlo_sweep0"]
 
 
 class LevelInfo(ctypes.Structure):

@@ -867,10 +867,10 @@ void nlo_cycle(hmg_ctx* c, const CycleCfg& cfg, const double* b, double* out, cu
   const bool single = cfg.nlev == 0;
   const int npre = single ? cfg.n_coarse : cfg.nu_pre;
   if (single && npre == 1) {
-    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, nullptr, out, cfg.omega, s));
+    LAUNCH(c, HMG_K_NLO_SWEEP0, 0, s, launch_nlo_sweep(X, nz, b, nullptr, out, cfg.omega, s));
     return;
   }
-  LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, nullptr, X.ua, cfg.omega, s));
+  LAUNCH(c, HMG_K_NLO_SWEEP0, 0, s, launch_nlo_sweep(X, nz, b, nullptr, X.ua, cfg.omega, s));
   double* cur = X.ua;
   double* nxt = X.ub;
   for (int i = 1; i < npre; ++i) {
@@ -1386,7 +1386,7 @@ const char* hmg_kernel_name(int kernel) {
   static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",     "prolong",  "resid_restrict", "apply",
                                            "dot",    "update_xr", "update_p", "layout",         "resid_sq",
                                            "assembly", "theta_grad", "ortho",    "nlo_sweep",      "nlo_resid",
-                                           "nlo_apply"};
+                                           "nlo_apply", "nlo_sweep0"};
   return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
 }
 

@@ -8,6 +8,7 @@ adjoint gradients against the oracle and central differences in 32 seeded
 directions.  r7x128 (42M cells): the oracle cannot solve it in seconds, so
 properties that hold at any size are checked (row sums = cell volumes from
 the oracle's mesh, symmetry, converged true residuals, both forms agree).
+r4x64 at next-to-lowest order: the same kind of properties.
 """
 import numpy as np
 import pytest
@@ -180,4 +181,41 @@ def test_velocity_pressure_system_full_size():
     assert i64["true_rel_residual"] < 2e-8 and im["true_rel_residual"] < 2e-8
     assert float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64)) < 1e-6
     assert float(torch.linalg.norm(pm - p64) / torch.linalg.norm(p64)) < 1e-6
+    h.close()
+
+
+def test_nlo_full_size_properties():
+    """r4x64 at next-to-lowest order (Table "GridSetup": 5,120 columns x 64
+    layers, 2.0 M pressure unknowns): the oracle cannot assemble and solve it
+    in seconds, so properties that hold at any size are checked: H^ is
+    symmetric; H^ 1 = M3 1 = |K| / 6 per unknown, with |K| = A_T(rho_l) dz
+    from the flat triangles of the exported vertices; the V-cycle is symmetric
+    and positive; both V-cycle forms converge to the same solution."""
+    w = gi.WORKLOADS["r4x64nlo"]
+    r, nz = w["refinement"], w["nlayers"]
+    h = hmg.Hierarchy(r, nz, w["nlevels"])
+    h.assemble()
+    n = h.nlo_size()
+    g = torch.Generator(device=DEV).manual_seed(23)
+    x = torch.randn(n, generator=g, dtype=torch.float64, device=DEV)
+    y = torch.randn(n, generator=g, dtype=torch.float64, device=DEV)
+    xHy, yHx = float(torch.dot(x, h.nlo_apply(y))), float(torch.dot(y, h.nlo_apply(x)))
+    assert xHy == pytest.approx(yHx, rel=1e-12)
+    V = h.export_vertices(0)
+    A1 = 0.5 * np.linalg.norm(np.cross(V[:, 1] - V[:, 0], V[:, 2] - V[:, 0]), axis=1)
+    prm = helmholtz.Params(refinement=r, nlayers=nz)
+    vol = A1[:, None] * prm.rho()[None, :] ** 2 * prm.dz
+    ones = torch.ones(n, dtype=torch.float64, device=DEV)
+    got = h.nlo_apply(ones).cpu().numpy().reshape(-1, nz, 6)
+    assert np.allclose(got, vol[:, :, None] / 6.0, rtol=1e-8)
+    Vx, Vy = h.nlo_vcycle(x), h.nlo_vcycle(y)
+    assert float(torch.dot(Vx, y)) == pytest.approx(float(torch.dot(x, Vy)), rel=1e-10)
+    assert float(torch.dot(x, Vx)) > 0
+    b = torch.tensor(gi.nlo_rhs(n), dtype=torch.float64, device=DEV)
+    x64, i64 = h.nlo_solve(b, rtol=1e-8)
+    xm, im = h.nlo_solve(b, rtol=1e-8, precision="mixed")
+    assert i64["converged"] == 1 and im["converged"] == 1
+    assert i64["true_rel_residual"] < 2e-8 and im["true_rel_residual"] < 2e-8
+    assert i64["iterations"] <= 40
+    assert float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)) < 1e-6
     h.close()
