@@ -282,10 +282,11 @@ def cpu_baseline_subprocess(workload, iterations):
 
 # NLO column-block sweep, per cell: three 6 x 6 blocks of coefficients (L_l,
 # omega Dt_l^-1, L_(l+1)^T), b, u, u' and the forward results written and read
-# back (6 unknowns each); three neighbour blocks, the forward and backward
-# block products and the relaxation: 6 x (18 + 6 + 12 + 1) FMA.
+# back (6 unknowns each); the three neighbour blocks (each a 3 x 3 horizontal
+# factor times the fixed 2 x 2 vertical one: 66 FMA), the forward and backward
+# block products (36 + 72 FMA) and the relaxation (6 FMA): 180 FMA.
 NLO_SWEEP_BYTES_PER_CELL = 3 * 36 * 8 + 5 * 6 * 8
-NLO_SWEEP_FLOPS_PER_CELL = 2 * 6 * (18 + 6 + 12 + 1)
+NLO_SWEEP_FLOPS_PER_CELL = 2 * (66 + 36 + 72 + 6)
 
 
 def nlo_section(args, world, dev, stream, hbm):

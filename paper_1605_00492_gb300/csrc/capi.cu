@@ -825,7 +825,7 @@ void ensure_nlo(hmg_ctx* c) {
     X.Lf = dalloc<double>(c, cw);
     X.Di = dalloc<double>(c, cw);
     X.Lb = dalloc<double>(c, cw);
-    X.Nb = dalloc<double>(c, (size_t)X.nt * 3 * 6 * 32);
+    X.Nb = dalloc<double>(c, (size_t)X.nt * 3 * 3 * 32);
     X.nb = dalloc<int>(c, (size_t)X.nt * 3 * 32);
     for (double** v : {&X.b, &X.x, &X.t1, &X.t2, &X.w, &X.ua, &X.ub}) *v = dalloc<double>(c, X.n);
     X.allocated = true;

@@ -136,6 +136,9 @@ void launch_mixed_layout(const Level& L, const MixedSys& M, bool to_tiled, const
 struct NloHost {
   int nc = 0, nz = 0;
   std::vector<double> diag, sub, nbr;
+  // nbr = nbr3 (x) Z2 with Z2 = [[5, 4], [4, 5]] / 12 (the vertical DG1
+  // factor): nbr3[(3 c + k) * 9 + 3 j + j'] is the horizontal factor
+  std::vector<double> nbr3;
 };
 NloHost nlo_assemble_host(const std::vector<double>& verts, const std::vector<int32_t>& nbr, int nc, int nz,
                           const Phys& ph);
@@ -150,9 +153,11 @@ constexpr int NLO_TILE = 5;   // columns per warp: lanes 6 c5 + u, lanes 30 and 
 // (tile, layer), index ((t * nz + l) * 6 + e) * 32 + lane = entry (u, e) of
 // the lane's cell: Ad the diagonal block, Cs the sub-diagonal block, Cu the
 // super-diagonal block (C_(l+1)^T), Lf the forward multipliers L_l, Di
-// omega Dt_l^-1, Lb the backward multipliers L_(l+1)^T.  Nb: 6 rows of 32 per
-// (tile, edge k); nb: per (tile, edge k, lane) the offset of the neighbour
-// column's row 0 plus its 6 c5.
+// omega Dt_l^-1, Lb the backward multipliers L_(l+1)^T.  Nb: 3 rows of 32 per
+// (tile, edge k): row j' holds, in lane 6 c5 + 2 j + m, entry (j, j') of the
+// horizontal factor of the neighbour block (the block is that factor times
+// Z2 = [[5, 4], [4, 5]] / 12 over (m, m')); nb: per (tile, edge k, lane) the
+// offset of the neighbour column's row 0 plus its 6 c5.
 struct NloSys {
   bool ready = false;        // coefficients of the current assembly uploaded
   bool allocated = false;

@@ -211,6 +211,7 @@ NloHost nlo_assemble_host(const std::vector<double>& verts, const std::vector<in
   out.diag.assign((size_t)nc * nz * 36, 0.0);
   out.sub.assign((size_t)nc * nz * 36, 0.0);
   out.nbr.assign((size_t)nc * 3 * 36, 0.0);
+  out.nbr3.assign((size_t)nc * 3 * 9, 0.0);
   const double dz = ph.dz;
 
   // horizontal energies hm[c][a] = int_T |v_a|^2 on the unit-sphere flat triangle
@@ -267,6 +268,8 @@ NloHost nlo_assemble_host(const std::vector<double>& verts, const std::vector<in
           }
       }
       double* blk = &out.nbr[((size_t)c * 3 + k) * 36];
+      for (int j = 0; j < 3; ++j)
+        for (int jj = 0; jj < 3; ++jj) out.nbr3[((size_t)c * 3 + k) * 9 + 3 * j + jj] = ph.wc2 * dz * nb[j][jj];
       for (int u = 0; u < 6; ++u)
         for (int uu = 0; uu < 6; ++uu) blk[u * 6 + uu] = ph.wc2 * dz * nb[u / 2][uu / 2] * Z2[u % 2][uu % 2];
     }
@@ -363,7 +366,7 @@ void nlo_pack_host(const NloHost& H, const std::vector<double>& Lf, const std::v
   const int nt = nc / NLO_TILE;
   const size_t cells = (size_t)nt * nz * 6 * 32;
   for (auto* v : {Ad, Cs, Cu, Lft, Dit, Lb}) v->assign(cells, 0.0);
-  Nb->assign((size_t)nt * 3 * 6 * 32, 0.0);
+  Nb->assign((size_t)nt * 3 * 3 * 32, 0.0);
   nb->assign((size_t)nt * 3 * 32, 0);
   for (int c = 0; c < nc; ++c) {
     const int t = c / NLO_TILE, c5 = c % NLO_TILE;
@@ -387,8 +390,8 @@ void nlo_pack_host(const NloHost& H, const std::vector<double>& Lf, const std::v
       const int n = nbr[3 * c + k];
       for (int u = 0; u < 6; ++u) {
         (*nb)[((size_t)t * 3 + k) * 32 + 6 * c5 + u] = (n / NLO_TILE) * nz * 32 + 6 * (n % NLO_TILE);
-        for (int e = 0; e < 6; ++e)
-          (*Nb)[(((size_t)t * 3 + k) * 6 + e) * 32 + 6 * c5 + u] = H.nbr[((size_t)c * 3 + k) * 36 + 6 * u + e];
+        for (int jj = 0; jj < 3; ++jj)
+          (*Nb)[(((size_t)t * 3 + k) * 3 + jj) * 32 + 6 * c5 + u] = H.nbr3[((size_t)c * 3 + k) * 9 + 3 * (u / 2) + jj];
       }
     }
   }
