@@ -16,10 +16,18 @@ Prints one JSON object with:
                 81,920 x 64 cells, Courant number 8 (the convergence history
                 of Sec. 6);
 * ``breakdown`` per-level, per-kernel device time of one multigrid solve
-                (the per-level breakdown of Table "Multigrid breakdown").
+                (the per-level breakdown of Table "Multigrid breakdown");
+* ``nlo``       next-to-lowest order on 5,120 x 64 cells (Table "GridSetup"):
+                GMRES(30) iterations and solve time to 1e-5 with the
+                multigrid (NLO level, p-coarsening, 4 lowest-order levels)
+                and with the single-level method, for Courant numbers 2..32
+                (Table "SingleNodePerformance" and Fig. "Algorithmic
+                scaling", NLO rows), and the per-kernel breakdown of one
+                multigrid solve.
 
-Right-hand sides are the seeded N(0,1) fields of ``hmg_inputs``; every solve
-runs to ||r|| / ||b|| < 1e-8 from x = 0.
+Right-hand sides are the seeded N(0,1) fields of ``hmg_inputs``; every
+lowest-order solve runs to ||r|| / ||b|| < 1e-8 from x = 0, every NLO solve
+to the paper's 1e-5.
 """
 import argparse
 import json
@@ -106,19 +114,50 @@ def breakdown(refinement=6, nlayers=64, nlevels=5):
     return out
 
 
+def nlo(cfls=(2, 8, 32), refinement=4, nlayers=64, nlevels=4):
+    h = hmg.Hierarchy(refinement, nlayers, nlevels)
+    b = torch.tensor(gi.nlo_rhs(6 * gi.ncells(refinement, nlayers)), device=DEV)
+    out = {"cfl": []}
+    for cfl in cfls:
+        h.assemble(nu_cfl=cfl)
+        row = {"nu_cfl": cfl}
+        for name, levels in (("multigrid", 0), ("single_level", 1)):
+            kw = dict(rtol=1e-5, restart=30, levels=levels, max_iter=3000)
+            h.nlo_solve(b, raise_on_failure=False, **kw)
+            torch.cuda.synchronize()
+            _, info = h.nlo_solve(b, raise_on_failure=False, **kw)
+            row[name] = {"iterations": info["iterations"], "solve_ms": round(info["solve_ms"], 3),
+                         "converged": info["converged"]}
+        out["cfl"].append(row)
+    h.assemble()
+    h.nlo_solve(b, rtol=1e-5)
+    h.profile_start()
+    _, info = h.nlo_solve(b, rtol=1e-5)
+    rec = h.profile_stop()
+    out["breakdown"] = {"iterations": info["iterations"],
+                        "kernels": {f"{k}@{lev}": {"launches": n, "ms": round(ms, 4)}
+                                    for (k, lev), (n, ms) in sorted(rec.items(), key=lambda kv: (kv[0][1], kv[0][0]))}}
+    h.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--quick", action="store_true", help="smaller shells (refinement 5) and fewer Courant numbers")
+    ap.add_argument("--only", choices=["grid", "cfl", "history", "breakdown", "nlo"], default=None,
+                    help="run one experiment")
     args = ap.parse_args()
     if not torch.cuda.is_available():
         raise SystemExit("a CUDA device is required")
     r = 5 if args.quick else 6
-    res = {
-        "grid": grid_independence([3, 4, 5] if args.quick else [3, 4, 5, 6, 7]),
-        "cfl": cfl_sweep([2, 8, 32] if args.quick else [2, 4, 8, 16, 32, 64], refinement=r),
-        "history": history(refinement=r),
-        "breakdown": breakdown(refinement=r),
+    runs = {
+        "grid": lambda: grid_independence([3, 4, 5] if args.quick else [3, 4, 5, 6, 7]),
+        "cfl": lambda: cfl_sweep([2, 8, 32] if args.quick else [2, 4, 8, 16, 32, 64], refinement=r),
+        "history": lambda: history(refinement=r),
+        "breakdown": lambda: breakdown(refinement=r),
+        "nlo": lambda: nlo((8,) if args.quick else (2, 8, 32)),
     }
+    res = {k: f() for k, f in runs.items() if args.only in (None, k)}
     print(json.dumps(res))
 
 
