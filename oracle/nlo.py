@@ -213,6 +213,34 @@ class NLOOperator:
         return 6 * self.ncols * self.nlayers
 
 
+def horizontal_dofs(mesh, nz):
+    """Global horizontal velocity unknowns as a list of (column, local BDFM1
+    unknown a, base, sign): the unknown (layer l, DG1 node b in z) is global
+    number base + 2 l + b and equals sign times the column's local function.
+    Edge unknowns (edge E, point q) come first, E in the order of
+    helmholtz.horizontal_faces, with the outward normal of the edge's first
+    (lower-numbered) column; the point q of the second column is the one at
+    the same position on the shared edge.  Interior unknowns (column, k)
+    follow.  Returns (owner list, number of edge unknowns, total)."""
+    edges = helmholtz.horizontal_faces(mesh)
+    ne = edges.shape[0]
+    nhe = ne * 2 * nz * 2
+    owner = []
+    for E, (t, k, tn, kn) in enumerate(edges):
+        ft, fn = mesh.faces[t], mesh.faces[tn]
+        same = ft[(k + 1) % 3] == fn[(kn + 1) % 3] and ft[(k + 2) % 3] == fn[(kn + 2) % 3]
+        rev = ft[(k + 1) % 3] == fn[(kn + 2) % 3] and ft[(k + 2) % 3] == fn[(kn + 1) % 3]
+        assert same != rev
+        for q in range(2):
+            qn = q if same else 1 - q
+            owner.append((t, 2 * k + q, (E * 2 + q) * nz * 2, 1.0))
+            owner.append((tn, 2 * kn + qn, (E * 2 + q) * nz * 2, -1.0))
+    for c in range(mesh.ncols):
+        for k in range(3):
+            owner.append((c, 6 + k, nhe + (c * 3 + k) * nz * 2, 1.0))
+    return owner, nhe, nhe + mesh.ncols * 3 * nz * 2
+
+
 def assemble_nlo(mesh, prm):
     """H^ of Eq. (Preconditioner) for the NLO spaces on one mesh (theta = 1)."""
     nc, nz = mesh.ncols, prm.nlayers
@@ -236,24 +264,8 @@ def assemble_nlo(mesh, prm):
 
     # horizontal velocity: global edge dofs (edge E, point q, layer, b) with the
     # normal of the lower-numbered face, then interior dofs (col, k, layer, b)
-    edges = helmholtz.horizontal_faces(mesh)
-    ne = edges.shape[0]
-    nhe = ne * 2 * nz * 2
-    nhf = nhe + nc * 3 * nz * 2
+    owner, nhe, nhf = horizontal_dofs(mesh, nz)
     lay = np.arange(nz)
-    owner = []   # (column, local unknown a, first global dof of (layer, b) = base + 2 layer + b, sign)
-    for E, (t, k, tn, kn) in enumerate(edges):
-        ft, fn = mesh.faces[t], mesh.faces[tn]
-        same = ft[(k + 1) % 3] == fn[(kn + 1) % 3] and ft[(k + 2) % 3] == fn[(kn + 2) % 3]
-        rev = ft[(k + 1) % 3] == fn[(kn + 2) % 3] and ft[(k + 2) % 3] == fn[(kn + 1) % 3]
-        assert same != rev
-        for q in range(2):
-            qn = q if same else 1 - q
-            owner.append((t, 2 * k + q, (E * 2 + q) * nz * 2, 1.0))
-            owner.append((tn, 2 * kn + qn, (E * 2 + q) * nz * 2, -1.0))
-    for c in range(nc):
-        for k in range(3):
-            owner.append((c, 6 + k, nhe + (c * 3 + k) * nz * 2, 1.0))
     rows, cols, vals = [], [], []
     mh = np.zeros(nhf)
     for (c, a, base, sgn) in owner:

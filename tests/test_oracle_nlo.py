@@ -52,7 +52,7 @@ def _dofs_of(T, P, field):
     for k in range(3):
         i, j = (k + 1) % 3, (k + 2) % 3
         length = np.linalg.norm(P[j] - P[i])
-        for q, s in enumerate(nlo.S_POINTS):
+        for q, s in enumerate((1.0 / 3.0, 2.0 / 3.0)):      # the reading: the points 1/3 and 2/3 of the edge
             out[2 * k + q] = length * np.dot(field(P[i] + s * (P[j] - P[i])), T.normals[k])
         Wk = lambda x: _bary(P, x)[i] * T.grads[j] - _bary(P, x)[j] * T.grads[i]
         out[6 + k] = sum(wq * np.dot(field(x), Wk(x)) for x, wq in zip(pts, wts))
@@ -320,3 +320,107 @@ def test_nlo_smoother_exact_for_decoupled_columns(tiny):
     b = RNG.standard_normal(nop.n)
     u = nlo.smooth(dec, np.zeros(nop.n), b, 1.0)
     assert np.linalg.norm(nop.Hz @ u - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_horizontal_unknowns_have_continuous_normal_flux():
+    """Each global edge unknown is one function on the two columns of its
+    edge: its flux density across the edge (the normal component in each
+    flat triangle's own plane, oriented from the first column to the second)
+    is the same from both sides at every point of the edge (a swapped point
+    or a wrong sign breaks this)."""
+    m = mesh.hierarchy(1, 1)[0]
+    owner, nhe, _ = nlo.horizontal_dofs(m, 1)
+    by_base = {}
+    for (c, a, base, sgn) in owner:
+        if base < nhe:
+            by_base.setdefault(base, []).append((c, a, sgn))
+    tri = {}
+    for base, sides in by_base.items():
+        assert len(sides) == 2
+        (c0, a0, s0), (c1, a1, s1) = sides
+        for c in (c0, c1):
+            if c not in tri:
+                tri[c] = nlo.triangle_bdfm(m.verts[m.faces[c]])
+        k0 = a0 // 2
+        i, j = (k0 + 1) % 3, (k0 + 2) % 3
+        P = m.verts[m.faces[c0]]
+        n0, n1 = tri[c0].normals[k0], tri[c1].normals[a1 // 2]   # outward normals of each column
+        for s in (0.0, 0.3, 0.7, 1.0):
+            x = P[i] + s * (P[j] - P[i])
+            f0 = s0 * np.dot(nlo.evaluate(tri[c0].basis[a0], _bary(P, x)), n0)
+            f1 = -s1 * np.dot(nlo.evaluate(tri[c1].basis[a1], _bary(m.verts[m.faces[c1]], x)), n1)
+            assert f0 == pytest.approx(f1, abs=1e-10 * (1 + abs(f0)))
+
+
+def test_nlo_matrices_by_prism_quadrature():
+    """Entries of D_h, D_z and the lumped masses of the assembled operator
+    against brute-force integration of the basis functions over the physical
+    prisms: the triangle scaled to the mid-layer radius, Gauss rules in the
+    plane and in z, divergences by central differences."""
+    ms = mesh.hierarchy(0, 1)
+    m = ms[0]
+    prm = helmholtz.Params(refinement=0, nlayers=2)
+    nz, dz = prm.nlayers, prm.dz
+    nop = nlo.assemble_nlo(m, prm)
+    owner, nhe, nhf = nlo.horizontal_dofs(m, nz)
+    rho = prm.rho()
+    g, w = np.polynomial.legendre.leggauss(4)
+    zq, zw = 0.5 * (g + 1.0) * dz, 0.5 * w * dz                      # Gauss points on one layer
+    eta = lambda z: np.array([1.0 - z / dz, z / dz])                  # DG1 nodal in z
+    s_ = lambda z: z / dz
+    zeta = lambda z: np.array([(1 - s_(z)) * (1 - 2 * s_(z)), 4 * s_(z) * (1 - s_(z)), s_(z) * (2 * s_(z) - 1)])
+    h = 1e-6
+    rng = np.random.default_rng(5)
+    Dh, Dz = nop.Dh.tocsc(), nop.Dz.tocsc()
+    # horizontal unknowns: mass and divergence pairings
+    for (c, a, base, sgn) in [owner[i] for i in rng.choice(len(owner), 12, replace=False)]:
+        layer, b = rng.integers(nz), rng.integers(2)
+        f = base + 2 * layer + b
+        mass_q = 0.0
+        for (c2, a2, base2, sgn2) in owner:
+            if base2 != base:
+                continue
+            Pl = m.verts[m.faces[c2]] * rho[layer]
+            T = nlo.triangle_bdfm(Pl)
+            pts, wts = _quad_points(Pl)
+            hm = sum(wq * np.dot(nlo.evaluate(T.basis[a2], _bary(Pl, x)), nlo.evaluate(T.basis[a2], _bary(Pl, x)))
+                     for x, wq in zip(pts, wts))
+            mass_q += hm * sum(wz * (eta(z)[b] / dz) ** 2 for z, wz in zip(zq, zw))
+            e1 = (Pl[1] - Pl[0]) / np.linalg.norm(Pl[1] - Pl[0])
+            e2 = np.cross(np.cross(Pl[1] - Pl[0], Pl[2] - Pl[0]), e1)
+            e2 /= np.linalg.norm(e2)
+            hx = 1e-5 * np.linalg.norm(Pl[1] - Pl[0])     # well above the spacing of doubles near |x| ~ R
+            v = lambda x: sgn2 * nlo.evaluate(T.basis[a2], _bary(Pl, x))
+            div = lambda x: (np.dot(v(x + hx * e1) - v(x - hx * e1), e1)
+                             + np.dot(v(x + hx * e2) - v(x - hx * e2), e2)) / (2 * hx)
+            for jv in range(3):
+                for mm in range(2):
+                    q = sum(wq * _bary(Pl, x)[jv] * div(x) for x, wq in zip(pts, wts)) * \
+                        sum(wz * eta(z)[mm] * eta(z)[b] / dz for z, wz in zip(zq, zw))
+                    got = Dh[nlo.pdof(c2, layer, jv, mm, nz), f]
+                    assert got == pytest.approx(q, abs=1e-6 * max(1.0, abs(q)))
+        assert nop.mh[f] == pytest.approx(mass_q, rel=1e-9)
+    # vertical unknowns (column c, vertex i, node 1 .. 2 nz - 1)
+    nzn = 2 * nz - 1
+    for c in rng.choice(m.ncols, 4, replace=False):
+        for i in range(3):
+            for node in range(1, 2 * nz):
+                f = (c * 3 + i) * nzn + node - 1
+                mass_q = 0.0
+                for layer in range(nz):
+                    kz = node - 2 * layer
+                    if kz < 0 or kz > 2:
+                        continue
+                    Pl = m.verts[m.faces[c]] * rho[layer]
+                    area = 0.5 * np.linalg.norm(np.cross(Pl[1] - Pl[0], Pl[2] - Pl[0]))
+                    pts, wts = _quad_points(Pl)
+                    lam = [_bary(Pl, x) for x in pts]
+                    mass_q += sum(wq * (lb[i] / (2 * area)) ** 2 for lb, wq in zip(lam, wts)) * \
+                        sum(wz * zeta(z)[kz] ** 2 for z, wz in zip(zq, zw))
+                    for jv in range(3):
+                        for mm in range(2):
+                            dzeta = lambda z: (zeta(z + h * dz)[kz] - zeta(z - h * dz)[kz]) / (2 * h * dz)
+                            q = sum(wq * lb[jv] * lb[i] / (2 * area) for lb, wq in zip(lam, wts)) * \
+                                sum(wz * eta(z)[mm] * dzeta(z) for z, wz in zip(zq, zw))
+                            assert Dz[nlo.pdof(c, layer, jv, mm, nz), f] == pytest.approx(q, abs=1e-7 * max(1, abs(q)))
+                assert nop.mz[f] == pytest.approx(mass_q, rel=1e-9)
