@@ -828,6 +828,9 @@ void ensure_nlo(hmg_ctx* c) {
     X.Nb = dalloc<double>(c, (size_t)X.nt * 3 * 3 * 32);
     X.nb = dalloc<int>(c, (size_t)X.nt * 3 * 32);
     for (double** v : {&X.b, &X.x, &X.t1, &X.t2, &X.w, &X.ua, &X.ub}) *v = dalloc<double>(c, X.n);
+    for (float** v : {&X.Ad32, &X.Cs32, &X.Cu32, &X.Lf32, &X.Di32, &X.Lb32}) *v = dalloc<float>(c, cw);
+    X.Nb32 = dalloc<float>(c, (size_t)X.nt * 3 * 3 * 32);
+    for (float** v : {&X.b32, &X.w32, &X.ua32, &X.ub32}) *v = dalloc<float>(c, X.n);
     X.allocated = true;
   }
   const NloHost H = nlo_assemble_host(L.verts_host, L.nbr_host, L.nc, L.nz, c->ph);
@@ -839,13 +842,20 @@ void ensure_nlo(hmg_ctx* c) {
   auto up = [](void* dst, const void* src, size_t bytes) {
     cuda_ok(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "NLO upload");
   };
-  up(X.Ad, Ad.data(), Ad.size() * sizeof(double));
-  up(X.Cs, Cs.data(), Cs.size() * sizeof(double));
-  up(X.Cu, Cu.data(), Cu.size() * sizeof(double));
-  up(X.Lf, Lft.data(), Lft.size() * sizeof(double));
-  up(X.Di, Dit.data(), Dit.size() * sizeof(double));
-  up(X.Lb, Lb.data(), Lb.size() * sizeof(double));
-  up(X.Nb, Nb.data(), Nb.size() * sizeof(double));
+  // FP64 tables and their FP32 copies (rounded to nearest)
+  std::vector<float> f32;
+  auto up2 = [&](double* d64, float* d32, const std::vector<double>& v) {
+    up(d64, v.data(), v.size() * sizeof(double));
+    f32.assign(v.begin(), v.end());
+    up(d32, f32.data(), f32.size() * sizeof(float));
+  };
+  up2(X.Ad, X.Ad32, Ad);
+  up2(X.Cs, X.Cs32, Cs);
+  up2(X.Cu, X.Cu32, Cu);
+  up2(X.Lf, X.Lf32, Lft);
+  up2(X.Di, X.Di32, Dit);
+  up2(X.Lb, X.Lb32, Lb);
+  up2(X.Nb, X.Nb32, Nb);
   up(X.nb, nb.data(), nb.size() * sizeof(int));
   X.ready = true;
 }
@@ -858,34 +868,51 @@ CycleCfg nlo_cfg(const hmg_ctx* c, int nu_pre, int nu_post, int n_coarse, int le
   return cfg;
 }
 
-// out <- V b on the NLO level (tiled NLO vectors, zero initial guess); out
-// must not be nlo.ua or nlo.ub.
+// out <- V b on the NLO level (tiled NLO FP64 vectors, zero initial guess);
+// out must not be one of the NLO work vectors.  The mixed form runs the NLO
+// level in FP32 unless it is the only level (the coarsest level stays FP64,
+// as in the lowest-order cycle).
 void nlo_cycle(hmg_ctx* c, const CycleCfg& cfg, const double* b, double* out, cudaStream_t s) {
   NloSys& X = c->nlo;
   Level& L0 = c->lv[0];
   const int nz = L0.nz;
   const bool single = cfg.nlev == 0;
+  const int dt = (cfg.mixed && !single) ? HMG_FP32 : HMG_FP64;
   const int npre = single ? cfg.n_coarse : cfg.nu_pre;
   if (single && npre == 1) {
-    LAUNCH(c, HMG_K_NLO_SWEEP0, 0, s, launch_nlo_sweep(X, nz, b, nullptr, out, cfg.omega, s));
+    LAUNCH(c, HMG_K_NLO_SWEEP0, 0, s,
+           launch_nlo_sweep(X, nz, dt, b, HMG_FP64, nullptr, nullptr, out, HMG_FP64, cfg.omega, s));
     return;
   }
-  LAUNCH(c, HMG_K_NLO_SWEEP0, 0, s, launch_nlo_sweep(X, nz, b, nullptr, X.ua, cfg.omega, s));
-  double* cur = X.ua;
-  double* nxt = X.ub;
+  void* A = dt == HMG_FP64 ? (void*)X.ua : (void*)X.ua32;
+  void* B = dt == HMG_FP64 ? (void*)X.ub : (void*)X.ub32;
+  const void* bl = dt == HMG_FP64 ? (const void*)b : (const void*)X.b32;
+  LAUNCH(c, HMG_K_NLO_SWEEP0, 0, s,
+         launch_nlo_sweep(X, nz, dt, b, HMG_FP64, dt == HMG_FP32 ? X.b32 : nullptr, nullptr, A, dt, cfg.omega, s));
+  void* cur = A;
+  void* nxt = B;
   for (int i = 1; i < npre; ++i) {
     const bool last = single && i == npre - 1;
-    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, cur, last ? out : nxt, cfg.omega, s));
+    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s,
+           launch_nlo_sweep(X, nz, dt, bl, dt, nullptr, cur, last ? (void*)out : nxt, last ? HMG_FP64 : dt,
+                            cfg.omega, s));
     if (last) return;
     std::swap(cur, nxt);
   }
-  if (L0.ncp > L0.nc) cuda_ok(cudaMemsetAsync(L0.b64, 0, (size_t)L0.Np * sizeof(double), s), "memset");
-  LAUNCH(c, HMG_K_NLO_RESID, 0, s, launch_nlo_resid_restrict(X, L0, b, cur, L0.b64, s));
-  cycle(c, cfg, 0, L0.b64, HMG_FP64, L0.ux64, HMG_FP64, s);
-  LAUNCH(c, HMG_K_PROLONG, 0, s, launch_nlo_prolong(X, L0, cur, L0.ux64, s));
+  const int cdt = level_dt(c, cfg, 0);
+  void* bc = work(L0, cdt, 2);
+  void* ec = cdt == HMG_FP64 ? (void*)L0.ux64 : (void*)L0.ux32;
+  if (L0.ncp > L0.nc)
+    cuda_ok(cudaMemsetAsync(bc, 0, (size_t)L0.Np * (cdt == HMG_FP64 ? sizeof(double) : sizeof(float)), s),
+            "memset");
+  LAUNCH(c, HMG_K_NLO_RESID, 0, s, launch_nlo_resid_restrict(X, L0, dt, bl, cur, bc, cdt, s));
+  cycle(c, cfg, 0, bc, cdt, ec, cdt, s);
+  LAUNCH(c, HMG_K_PROLONG, 0, s, launch_nlo_prolong(X, L0, dt, cur, ec, cdt, s));
   for (int i = 0; i < cfg.nu_post; ++i) {
     const bool last = i == cfg.nu_post - 1;
-    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s, launch_nlo_sweep(X, nz, b, cur, last ? out : nxt, cfg.omega, s));
+    LAUNCH(c, HMG_K_NLO_SWEEP, 0, s,
+           launch_nlo_sweep(X, nz, dt, bl, dt, nullptr, cur, last ? (void*)out : nxt, last ? HMG_FP64 : dt,
+                            cfg.omega, s));
     std::swap(cur, nxt);
   }
 }

@@ -167,21 +167,29 @@ struct NloSys {
   double* Nb = nullptr;
   int* nb = nullptr;
   double *b = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr, *w = nullptr, *ua = nullptr, *ub = nullptr;
+  // FP32 copies for the mixed form, and its FP32 work vectors
+  float *Ad32 = nullptr, *Cs32 = nullptr, *Cu32 = nullptr, *Lf32 = nullptr, *Di32 = nullptr, *Lb32 = nullptr;
+  float* Nb32 = nullptr;
+  float *b32 = nullptr, *w32 = nullptr, *ua32 = nullptr, *ub32 = nullptr;
 };
 void nlo_pack_host(const NloHost& H, const std::vector<double>& Lf, const std::vector<double>& Dinv,
                    const std::vector<int32_t>& nbr, std::vector<double>* Ad, std::vector<double>* Cs,
                    std::vector<double>* Cu, std::vector<double>* Lft, std::vector<double>* Dit,
                    std::vector<double>* Lb, std::vector<double>* Nb, std::vector<int>* nb);
 void launch_nlo_layout(const NloSys& X, int nz, bool to_tiled, const double* src, double* dst, cudaStream_t s);
-void launch_nlo_apply(const NloSys& X, int nz, const double* x, double* y, cudaStream_t s);
-// bc (lowest-order level L0, TILED) = P^T (b - H^ u), P the embedding DG0 -> DG1
-void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, const double* b, const double* u, double* bc,
-                               cudaStream_t s);
-// uo = u + omega H^_z^-1 (b - H^ u); u == nullptr: from u = 0
-void launch_nlo_sweep(const NloSys& X, int nz, const double* b, const double* u, double* uo, double omega,
-                      cudaStream_t s);
-// u += P ec, ec on the lowest-order level L0 (TILED)
-void launch_nlo_prolong(const NloSys& X, const Level& L0, double* u, const double* ec, cudaStream_t s);
+void launch_nlo_apply(const NloSys& X, int nz, const double* x, double* y, cudaStream_t s);   // FP64
+// bc (lowest-order level L0, TILED, type bc_dt) = P^T (b - H^ u), P the
+// embedding DG0 -> DG1; b and u of type dt
+void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, int dt, const void* b, const void* u, void* bc,
+                               int bc_dt, cudaStream_t s);
+// uo = u + omega H^_z^-1 (b - H^ u) in type dt (u == nullptr: from u = 0);
+// b of type b_dt (FP64 with dt FP32 only from zero, then copied to bcopy if
+// given), uo of type uo_dt
+void launch_nlo_sweep(const NloSys& X, int nz, int dt, const void* b, int b_dt, void* bcopy, const void* u,
+                      void* uo, int uo_dt, double omega, cudaStream_t s);
+// u (type dt) += P ec, ec on the lowest-order level L0 (TILED, type ec_dt)
+void launch_nlo_prolong(const NloSys& X, const Level& L0, int dt, void* u, const void* ec, int ec_dt,
+                        cudaStream_t s);
 
 // ---- assembly (assemble.cu)
 void launch_geometry(const Level& L, cudaStream_t s);

@@ -11,7 +11,12 @@
 // column solve is the block L D L^T recurrence, forward then backward, with
 // the forward results kept in a scratch vector (same lane, same thread).  The
 // per-cell coefficients (three 6 x 6 blocks per kernel) are the dominant
-// memory traffic; the 6 x 6 products run on the FP64 pipe.
+// memory traffic; in FP64 the 6 x 6 products run on the FP64 pipe, which
+// bounds the kernels.  The mixed form runs the same kernels in FP32 (FP32
+// copies of the coefficients, FP32 work vectors), where the FP32 pipe leaves
+// them bound by memory.
+#include <stdexcept>
+
 #include "hmg_internal.h"
 
 namespace hmg {
@@ -21,21 +26,28 @@ namespace {
 constexpr int NW = 4;                       // warps per CTA
 constexpr unsigned FULL = 0xffffffffu;
 
+template <typename T>
 struct NloArgs {
   int nt, nz;
-  const double* __restrict__ Ad;
-  const double* __restrict__ Cs;
-  const double* __restrict__ Cu;
-  const double* __restrict__ Lf;
-  const double* __restrict__ Di;
-  const double* __restrict__ Lb;
-  const double* __restrict__ Nb;
+  const T* __restrict__ Ad;
+  const T* __restrict__ Cs;
+  const T* __restrict__ Cu;
+  const T* __restrict__ Lf;
+  const T* __restrict__ Di;
+  const T* __restrict__ Lb;
+  const T* __restrict__ Nb;
   const int* __restrict__ nb;
 };
 
-NloArgs args_of(const NloSys& X, int nz) {
-  return NloArgs{X.nt, nz, X.Ad, X.Cs, X.Cu, X.Lf, X.Di, X.Lb, X.Nb, X.nb};
+NloArgs<double> args_of(const NloSys& X, int nz, double) {
+  return NloArgs<double>{X.nt, nz, X.Ad, X.Cs, X.Cu, X.Lf, X.Di, X.Lb, X.Nb, X.nb};
 }
+NloArgs<float> args_of(const NloSys& X, int nz, float) {
+  return NloArgs<float>{X.nt, nz, X.Ad32, X.Cs32, X.Cu32, X.Lf32, X.Di32, X.Lb32, X.Nb32, X.nb};
+}
+
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // First lane of the lane's group of six (the padding lanes use group 4).
 __device__ __forceinline__ int group_base(int lane) {
@@ -48,14 +60,16 @@ __device__ __forceinline__ int group_base(int lane) {
 // The block is that factor times Z2 = [[5, 4], [4, 5]] / 12 over (m, m'), so
 // sum_k N_k x_k = (5 S_m + 4 S_(1-m)) / 12 with S_m = sum_k sum_j' H_k[j][j']
 // x_k[j', m]: 9 FMA per lane and the partner lane's S by one shuffle.
+template <typename T>
 struct Nbr {
-  double h[3][3];
+  T h[3][3];
   int base[3];
 };
 
 constexpr double Z_SELF = 5.0 / 12.0, Z_OTHER = 4.0 / 12.0;
 
-__device__ __forceinline__ void load_nbr(const NloArgs& A, int t, int lane, Nbr& n) {
+template <typename T>
+__device__ __forceinline__ void load_nbr(const NloArgs<T>& A, int t, int lane, Nbr<T>& n) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     n.base[k] = A.nb[(t * 3 + k) * 32 + lane] + (lane & 1);
@@ -65,86 +79,91 @@ __device__ __forceinline__ void load_nbr(const NloArgs& A, int t, int lane, Nbr&
 }
 
 // the nine neighbour values x_k[j', m] of the lane at layer l
-__device__ __forceinline__ void load_nbr_x(const Nbr& n, const double* __restrict__ x, int l, double (&v)[3][3]) {
+template <typename T>
+__device__ __forceinline__ void load_nbr_x(const Nbr<T>& n, const T* __restrict__ x, int l, T (&v)[3][3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double* xn = x + n.base[k] + (size_t)l * 32;
+    const T* xn = x + n.base[k] + (size_t)l * 32;
 #pragma unroll
     for (int jj = 0; jj < 3; ++jj) v[k][jj] = xn[2 * jj];
   }
 }
 
 // sum_k sum_j' H_k[j][j'] v[k][j']
-__device__ __forceinline__ double nbr_dot(const Nbr& n, const double (&v)[3][3]) {
-  double s = n.h[0][0] * v[0][0];
+template <typename T>
+__device__ __forceinline__ T nbr_dot(const Nbr<T>& n, const T (&v)[3][3]) {
+  T s = n.h[0][0] * v[0][0];
 #pragma unroll
-  for (int q = 1; q < 9; ++q) s = fma(n.h[q / 3][q % 3], v[q / 3][q % 3], s);
+  for (int q = 1; q < 9; ++q) s = fmx(n.h[q / 3][q % 3], v[q / 3][q % 3], s);
   return s;
 }
 
 // uo = u + omega H^_z^-1 (b - H^ u) = (1 - omega) u + omega H^_z^-1 (b - H^_h u)
 // (u = nullptr: from zero).  omega is folded into Di.  The operands of layer
-// l +- 1 are loaded while layer l is computed.
-template <bool FROM_ZERO>
-__global__ void __launch_bounds__(NW * 32) k_nlo_sweep(NloArgs A, const double* __restrict__ b,
-                                                       const double* __restrict__ u, double* __restrict__ uo,
-                                                       double* __restrict__ wbuf, double omega) {
+// l +- 1 are loaded while layer l is computed.  T: arithmetic, coefficients
+// and u; TB: b (converted to T, and copied to bcopy when given); TO: uo.
+template <typename T, bool FROM_ZERO, typename TB, typename TO>
+__global__ void __launch_bounds__(NW * 32) k_nlo_sweep(NloArgs<T> A, const TB* __restrict__ b,
+                                                       T* __restrict__ bcopy, const T* __restrict__ u,
+                                                       TO* __restrict__ uo, T* __restrict__ wbuf, T omega) {
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * NW + (threadIdx.x >> 5);
   if (t >= A.nt) return;   // warp-uniform
   const int g = group_base(lane);
   const size_t tile0 = (size_t)t * A.nz * 32;
   const int nz = A.nz;
-  Nbr n;
+  const T zs = T(Z_SELF), zo = T(Z_OTHER);
+  Nbr<T> n;
   if (!FROM_ZERO) load_nbr(A, t, lane, n);
   // forward: w_l = (b - H^_h u)_l - L_l w_(l-1)
-  double bq = b[tile0 + lane], vq[3][3], Lq[6];
+  T bq = T(b[tile0 + lane]), vq[3][3], Lq[6];
   if (!FROM_ZERO) load_nbr_x(n, u, 0, vq);
 #pragma unroll
-  for (int e = 0; e < 6; ++e) Lq[e] = 0.0;
-  double wprev = 0.0;
+  for (int e = 0; e < 6; ++e) Lq[e] = T(0);
+  T wprev = T(0);
   for (int l = 0; l < nz; ++l) {
     const size_t row = tile0 + (size_t)l * 32;
-    const double bl = bq;
-    double vl[3][3], Ll[6];
+    const T bl = bq;
+    T vl[3][3], Ll[6];
 #pragma unroll
     for (int q = 0; q < 9; ++q) vl[q / 3][q % 3] = vq[q / 3][q % 3];
 #pragma unroll
     for (int e = 0; e < 6; ++e) Ll[e] = Lq[e];
     if (l + 1 < nz) {   // prefetch layer l + 1
       const size_t rn = row + 32;
-      bq = b[rn + lane];
+      bq = T(b[rn + lane]);
       if (!FROM_ZERO) load_nbr_x(n, u, l + 1, vq);
 #pragma unroll
       for (int e = 0; e < 6; ++e) Lq[e] = A.Lf[rn * 6 + e * 32 + lane];
     }
-    double w = bl;
+    if (bcopy) bcopy[row + lane] = bl;
+    T w = bl;
     if (!FROM_ZERO) {
-      const double S = nbr_dot(n, vl);
-      const double Sp = __shfl_xor_sync(FULL, S, 1);
-      w = fma(-Z_SELF, S, w);
-      w = fma(-Z_OTHER, Sp, w);
+      const T S = nbr_dot(n, vl);
+      const T Sp = __shfl_xor_sync(FULL, S, 1);
+      w = fmx(-zs, S, w);
+      w = fmx(-zo, Sp, w);
     }
     if (l > 0) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) w = fma(-Ll[e], __shfl_sync(FULL, wprev, g + e), w);
+      for (int e = 0; e < 6; ++e) w = fmx(-Ll[e], __shfl_sync(FULL, wprev, g + e), w);
     }
     wbuf[row + lane] = w;
     wprev = w;
   }
   // backward: x_l = omega Dt_l^-1 w_l - L_(l+1)^T x_(l+1)
   const size_t rlast = tile0 + (size_t)(nz - 1) * 32;
-  double wq = wprev, uq = FROM_ZERO ? 0.0 : u[rlast + lane], Dq[6], Bq[6];
+  T wq = wprev, uq = FROM_ZERO ? T(0) : u[rlast + lane], Dq[6], Bq[6];
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     Dq[e] = A.Di[rlast * 6 + e * 32 + lane];
-    Bq[e] = 0.0;
+    Bq[e] = T(0);
   }
-  double xnext = 0.0;
+  T xnext = T(0);
   for (int l = nz - 1; l >= 0; --l) {
     const size_t row = tile0 + (size_t)l * 32;
-    const double wl = wq, ul = uq;
-    double Dl[6], Bl[6];
+    const T wl = wq, ul = uq;
+    T Dl[6], Bl[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
       Dl[e] = Dq[e];
@@ -160,16 +179,16 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_sweep(NloArgs A, const double* 
         Bq[e] = A.Lb[rp * 6 + e * 32 + lane];
       }
     }
-    double x = 0.0;
+    T x = T(0);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) x = fma(Dl[e], __shfl_sync(FULL, wl, g + e), x);
+    for (int e = 0; e < 6; ++e) x = fmx(Dl[e], __shfl_sync(FULL, wl, g + e), x);
     if (l < nz - 1) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) x = fma(-Bl[e], __shfl_sync(FULL, xnext, g + e), x);
+      for (int e = 0; e < 6; ++e) x = fmx(-Bl[e], __shfl_sync(FULL, xnext, g + e), x);
     }
-    double out = x;
-    if (!FROM_ZERO) out = fma(1.0 - omega, ul, x);
-    uo[row + lane] = lane < 30 ? out : 0.0;
+    T out = x;
+    if (!FROM_ZERO) out = fmx(T(1) - omega, ul, x);
+    uo[row + lane] = lane < 30 ? TO(out) : TO(0);
     xnext = x;
   }
 }
@@ -178,10 +197,10 @@ constexpr int LCH = 8;   // layers per warp in the layer-parallel kernels
 
 // RESID: bc[(c, l)] = sum over the cell's six unknowns of (b - H^ x);
 // otherwise y = H^ x.  One warp per (tile, chunk of LCH layers).
-template <bool RESID>
-__global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs A, const double* __restrict__ x,
-                                                    const double* __restrict__ b, double* __restrict__ y,
-                                                    double* __restrict__ bc, int nchunks) {
+template <typename T, bool RESID, typename TBC>
+__global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __restrict__ x,
+                                                    const T* __restrict__ b, T* __restrict__ y,
+                                                    TBC* __restrict__ bc, int nchunks) {
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * NW + (threadIdx.x >> 5);
   if (wid >= A.nt * nchunks) return;   // warp-uniform
@@ -190,40 +209,40 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs A, const double* __r
   const int l1 = min(nz, l0 + LCH);
   const int g = group_base(lane);
   const size_t tile0 = (size_t)t * nz * 32;
-  Nbr n;
+  Nbr<T> n;
   load_nbr(A, t, lane, n);
-  double xm = l0 > 0 ? x[tile0 + (size_t)(l0 - 1) * 32 + lane] : 0.0;
-  double x0 = x[tile0 + (size_t)l0 * 32 + lane];
+  T xm = l0 > 0 ? x[tile0 + (size_t)(l0 - 1) * 32 + lane] : T(0);
+  T x0 = x[tile0 + (size_t)l0 * 32 + lane];
   for (int l = l0; l < l1; ++l) {
     const size_t row = tile0 + (size_t)l * 32;
     const size_t crow = row * 6;
-    const double xp = l + 1 < nz ? x[row + 32 + lane] : 0.0;
-    double v[3][3];
+    const T xp = l + 1 < nz ? x[row + 32 + lane] : T(0);
+    T v[3][3];
     load_nbr_x(n, x, l, v);
-    const double S = nbr_dot(n, v);
-    const double Sp = __shfl_xor_sync(FULL, S, 1);
-    double acc = Z_SELF * S;
-    acc = fma(Z_OTHER, Sp, acc);
+    const T S = nbr_dot(n, v);
+    const T Sp = __shfl_xor_sync(FULL, S, 1);
+    T acc = T(Z_SELF) * S;
+    acc = fmx(T(Z_OTHER), Sp, acc);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) acc = fma(A.Ad[crow + e * 32 + lane], __shfl_sync(FULL, x0, g + e), acc);
+    for (int e = 0; e < 6; ++e) acc = fmx(A.Ad[crow + e * 32 + lane], __shfl_sync(FULL, x0, g + e), acc);
     if (l > 0) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc = fma(A.Cs[crow + e * 32 + lane], __shfl_sync(FULL, xm, g + e), acc);
+      for (int e = 0; e < 6; ++e) acc = fmx(A.Cs[crow + e * 32 + lane], __shfl_sync(FULL, xm, g + e), acc);
     }
     if (l + 1 < nz) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc = fma(A.Cu[crow + e * 32 + lane], __shfl_sync(FULL, xp, g + e), acc);
+      for (int e = 0; e < 6; ++e) acc = fmx(A.Cu[crow + e * 32 + lane], __shfl_sync(FULL, xp, g + e), acc);
     }
     if (RESID) {
-      const double r = lane < 30 ? b[row + lane] - acc : 0.0;
-      const double pair = r + __shfl_xor_sync(FULL, r, 1);           // the two unknowns of vertex j
-      const double s = pair + __shfl_sync(FULL, pair, g + 2) + __shfl_sync(FULL, pair, g + 4);
+      const T r = lane < 30 ? b[row + lane] - acc : T(0);
+      const T pair = r + __shfl_xor_sync(FULL, r, 1);           // the two unknowns of vertex j
+      const T sum = pair + __shfl_sync(FULL, pair, g + 2) + __shfl_sync(FULL, pair, g + 4);
       if (lane < 30 && lane == g) {
         const int c = t * NLO_TILE + lane / 6;
-        bc[(size_t)(c / TW) * TW * nz + (size_t)l * TW + (c % TW)] = s;
+        bc[(size_t)(c / TW) * TW * nz + (size_t)l * TW + (c % TW)] = TBC(sum);
       }
     } else {
-      y[row + lane] = lane < 30 ? acc : 0.0;
+      y[row + lane] = lane < 30 ? acc : T(0);
     }
     xm = x0;
     x0 = xp;
@@ -231,7 +250,8 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs A, const double* __r
 }
 
 // u += P ec: every unknown of a cell gets the cell's coarse value.
-__global__ void k_nlo_prolong(int64_t n, int nz, double* __restrict__ u, const double* __restrict__ ec) {
+template <typename T, typename TE>
+__global__ void k_nlo_prolong(int64_t n, int nz, T* __restrict__ u, const TE* __restrict__ ec) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int lane = (int)(i & 31);
@@ -239,7 +259,7 @@ __global__ void k_nlo_prolong(int64_t n, int nz, double* __restrict__ u, const d
   const int64_t tl = i >> 5;                 // t * nz + l
   const int l = (int)(tl % nz);
   const int64_t c = (tl / nz) * NLO_TILE + lane / 6;
-  u[i] += ec[(c / TW) * TW * nz + (int64_t)l * TW + (c % TW)];
+  u[i] += T(ec[(c / TW) * TW * nz + (int64_t)l * TW + (c % TW)]);
 }
 
 // NLO COLUMN ((c nz + l) 6 + u) <-> NLO tiles
@@ -269,26 +289,70 @@ void launch_nlo_layout(const NloSys& X, int nz, bool to_tiled, const double* src
 int chunks(int nz) { return (nz + LCH - 1) / LCH; }
 
 void launch_nlo_apply(const NloSys& X, int nz, const double* x, double* y, cudaStream_t s) {
-  k_nlo_op<false><<<warps_grid(X.nt * chunks(nz)), NW * 32, 0, s>>>(args_of(X, nz), x, nullptr, y, nullptr,
-                                                                    chunks(nz));
+  k_nlo_op<double, false, double><<<warps_grid(X.nt * chunks(nz)), NW * 32, 0, s>>>(
+      args_of(X, nz, 0.0), x, nullptr, y, nullptr, chunks(nz));
 }
 
-void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, const double* b, const double* u, double* bc,
-                               cudaStream_t s) {
-  k_nlo_op<true><<<warps_grid(X.nt * chunks(L0.nz)), NW * 32, 0, s>>>(args_of(X, L0.nz), u, b, nullptr, bc,
-                                                                      chunks(L0.nz));
-}
-
-void launch_nlo_sweep(const NloSys& X, int nz, const double* b, const double* u, double* uo, double omega,
-                      cudaStream_t s) {
-  if (u)
-    k_nlo_sweep<false><<<warps_grid(X.nt), NW * 32, 0, s>>>(args_of(X, nz), b, u, uo, X.w, omega);
+template <typename T>
+void resid_t(const NloSys& X, const Level& L0, const T* b, const T* u, void* bc, int bc_dt, cudaStream_t s) {
+  const int g = warps_grid(X.nt * chunks(L0.nz));
+  if (bc_dt == HMG_FP64)
+    k_nlo_op<T, true, double><<<g, NW * 32, 0, s>>>(args_of(X, L0.nz, T(0)), u, b, nullptr, (double*)bc,
+                                                   chunks(L0.nz));
   else
-    k_nlo_sweep<true><<<warps_grid(X.nt), NW * 32, 0, s>>>(args_of(X, nz), b, nullptr, uo, X.w, omega);
+    k_nlo_op<T, true, float><<<g, NW * 32, 0, s>>>(args_of(X, L0.nz, T(0)), u, b, nullptr, (float*)bc,
+                                                  chunks(L0.nz));
 }
 
-void launch_nlo_prolong(const NloSys& X, const Level& L0, double* u, const double* ec, cudaStream_t s) {
-  k_nlo_prolong<<<elem_grid(X.n), 256, 0, s>>>(X.n, L0.nz, u, ec);
+void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, int dt, const void* b, const void* u, void* bc,
+                               int bc_dt, cudaStream_t s) {
+  if (dt == HMG_FP64) resid_t(X, L0, (const double*)b, (const double*)u, bc, bc_dt, s);
+  else resid_t(X, L0, (const float*)b, (const float*)u, bc, bc_dt, s);
+}
+
+template <typename T, typename TB, typename TO>
+void sweep_t(const NloSys& X, int nz, const TB* b, T* bcopy, const T* u, TO* uo, T* w, double omega,
+             cudaStream_t s) {
+  if (u)
+    k_nlo_sweep<T, false, TB, TO><<<warps_grid(X.nt), NW * 32, 0, s>>>(args_of(X, nz, T(0)), b, bcopy, u, uo, w,
+                                                                      T(omega));
+  else
+    k_nlo_sweep<T, true, TB, TO><<<warps_grid(X.nt), NW * 32, 0, s>>>(args_of(X, nz, T(0)), b, bcopy, nullptr, uo,
+                                                                     w, T(omega));
+}
+
+void launch_nlo_sweep(const NloSys& X, int nz, int dt, const void* b, int b_dt, void* bcopy, const void* u,
+                      void* uo, int uo_dt, double omega, cudaStream_t s) {
+  if (dt == HMG_FP64) {
+    if (b_dt != HMG_FP64 || uo_dt != HMG_FP64 || bcopy) throw std::invalid_argument("NLO FP64 sweep: FP64 only");
+    sweep_t<double, double, double>(X, nz, (const double*)b, nullptr, (const double*)u, (double*)uo, X.w, omega, s);
+    return;
+  }
+  float* w = X.w32;
+  if (b_dt == HMG_FP64) {
+    if (u) throw std::invalid_argument("NLO FP32 sweep: an FP64 right-hand side only from zero");
+    if (uo_dt == HMG_FP64)
+      sweep_t<float, double, double>(X, nz, (const double*)b, (float*)bcopy, nullptr, (double*)uo, w, omega, s);
+    else
+      sweep_t<float, double, float>(X, nz, (const double*)b, (float*)bcopy, nullptr, (float*)uo, w, omega, s);
+  } else if (uo_dt == HMG_FP64) {
+    sweep_t<float, float, double>(X, nz, (const float*)b, nullptr, (const float*)u, (double*)uo, w, omega, s);
+  } else {
+    sweep_t<float, float, float>(X, nz, (const float*)b, nullptr, (const float*)u, (float*)uo, w, omega, s);
+  }
+}
+
+void launch_nlo_prolong(const NloSys& X, const Level& L0, int dt, void* u, const void* ec, int ec_dt,
+                        cudaStream_t s) {
+  const int g = elem_grid(X.n);
+  if (dt == HMG_FP64 && ec_dt == HMG_FP64)
+    k_nlo_prolong<double, double><<<g, 256, 0, s>>>(X.n, L0.nz, (double*)u, (const double*)ec);
+  else if (dt == HMG_FP32 && ec_dt == HMG_FP32)
+    k_nlo_prolong<float, float><<<g, 256, 0, s>>>(X.n, L0.nz, (float*)u, (const float*)ec);
+  else if (dt == HMG_FP32)
+    k_nlo_prolong<float, double><<<g, 256, 0, s>>>(X.n, L0.nz, (float*)u, (const double*)ec);
+  else
+    k_nlo_prolong<double, float><<<g, 256, 0, s>>>(X.n, L0.nz, (double*)u, (const float*)ec);
 }
 
 }  // namespace hmg

@@ -114,6 +114,20 @@ def oracle_solve(c, rtol):
     return _SOLVES[key]
 
 
+def test_nlo_vcycle_mixed_against_fp64_oracle():
+    """The mixed form runs the NLO level and the non-coarsest lowest-order
+    levels in FP32: against the FP64 oracle the V-cycle differs by the FP32
+    rounding of the column solves (stated bound 1e-4, as for the lowest
+    order), and a single-level mixed cycle is the FP64 one."""
+    c = case(3, 16, 3)
+    b = gi.nlo_rhs(c.nop.n)
+    z = c.oracle_order(c.h.nlo_vcycle(c.gpu(b), precision="mixed"))
+    assert rel_l2(z, nlo.vcycle(c.nop, c.lo, b)) < 1e-4
+    z1 = c.oracle_order(c.h.nlo_vcycle(c.gpu(b), precision="mixed", levels=1))
+    ref = nlo.smooth(c.nop, nlo.smooth(c.nop, np.zeros(c.nop.n), b, 0.8), b, 0.8)
+    assert rel_l2(z1, ref) < 1e-11
+
+
 @pytest.mark.parametrize("r,nz,L,rtol,orth", [(2, 8, 2, 1e-8, 1), (3, 16, 3, 1e-10, 2)])
 def test_nlo_solve_matches_oracle(r, nz, L, rtol, orth):
     c = case(r, nz, L)
