@@ -99,13 +99,22 @@ __device__ __forceinline__ T nbr_dot(const Nbr<T>& n, const T (&v)[3][3]) {
 }
 
 // uo = u + omega H^_z^-1 (b - H^ u) = (1 - omega) u + omega H^_z^-1 (b - H^_h u)
-// (u = nullptr: from zero).  omega is folded into Di.  The operands of layer
-// l +- 1 are loaded while layer l is computed.  T: arithmetic, coefficients
-// and u; TB: b (converted to T, and copied to bcopy when given); TO: uo.
+// (u = nullptr: from zero).  omega is folded into Di.  T: arithmetic,
+// coefficients and u; TB: b (converted to T, and copied to bcopy when given);
+// TO: uo.  The warp walks its layers as a serial recurrence, so the operands
+// of the next PF layers are kept in flight in registers (staged slots
+// refilled as they are consumed): PF = 1 in FP64, where the FP64 pipe bounds
+// the kernel, PF = 4 in FP32, where memory latency does.
+template <typename T>
+struct SweepPF {
+  static constexpr int value = sizeof(T) == 4 ? 4 : 1;
+};
+
 template <typename T, bool FROM_ZERO, typename TB, typename TO>
 __global__ void __launch_bounds__(NW * 32) k_nlo_sweep(NloArgs<T> A, const TB* __restrict__ b,
                                                        T* __restrict__ bcopy, const T* __restrict__ u,
                                                        TO* __restrict__ uo, T* __restrict__ wbuf, T omega) {
+  constexpr int PF = SweepPF<T>::value;
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * NW + (threadIdx.x >> 5);
   if (t >= A.nt) return;   // warp-uniform
@@ -115,81 +124,92 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_sweep(NloArgs<T> A, const TB* _
   const T zs = T(Z_SELF), zo = T(Z_OTHER);
   Nbr<T> n;
   if (!FROM_ZERO) load_nbr(A, t, lane, n);
-  // forward: w_l = (b - H^_h u)_l - L_l w_(l-1)
-  T bq = T(b[tile0 + lane]), vq[3][3], Lq[6];
-  if (!FROM_ZERO) load_nbr_x(n, u, 0, vq);
+  // forward: w_l = (b - H^_h u)_l - L_l w_(l-1); slot d holds layer l0 + d
+  T bq[PF], vq[PF][3][3], Lq[PF][6];
+  auto load_f = [&](int d, int l) {
+    const size_t row = tile0 + (size_t)l * 32;
+    bq[d] = T(b[row + lane]);
+    if (!FROM_ZERO) load_nbr_x(n, u, l, vq[d]);
 #pragma unroll
-  for (int e = 0; e < 6; ++e) Lq[e] = T(0);
+    for (int e = 0; e < 6; ++e) Lq[d][e] = l > 0 ? A.Lf[row * 6 + e * 32 + lane] : T(0);
+  };
+#pragma unroll
+  for (int d = 0; d < PF; ++d)
+    if (d < nz) load_f(d, d);
   T wprev = T(0);
-  for (int l = 0; l < nz; ++l) {
-    const size_t row = tile0 + (size_t)l * 32;
-    const T bl = bq;
-    T vl[3][3], Ll[6];
+  for (int l0 = 0; l0 < nz; l0 += PF) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) vl[q / 3][q % 3] = vq[q / 3][q % 3];
+    for (int d = 0; d < PF; ++d) {
+      const int l = l0 + d;
+      if (l >= nz) break;   // warp-uniform
+      const size_t row = tile0 + (size_t)l * 32;
+      const T bl = bq[d];
+      T vl[3][3], Ll[6];
 #pragma unroll
-    for (int e = 0; e < 6; ++e) Ll[e] = Lq[e];
-    if (l + 1 < nz) {   // prefetch layer l + 1
-      const size_t rn = row + 32;
-      bq = T(b[rn + lane]);
-      if (!FROM_ZERO) load_nbr_x(n, u, l + 1, vq);
+      for (int q = 0; q < 9; ++q) vl[q / 3][q % 3] = vq[d][q / 3][q % 3];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) Lq[e] = A.Lf[rn * 6 + e * 32 + lane];
+      for (int e = 0; e < 6; ++e) Ll[e] = Lq[d][e];
+      if (l + PF < nz) load_f(d, l + PF);   // refill the slot with layer l + PF
+      if (bcopy) bcopy[row + lane] = bl;
+      T w = bl;
+      if (!FROM_ZERO) {
+        const T S = nbr_dot(n, vl);
+        const T Sp = __shfl_xor_sync(FULL, S, 1);
+        w = fmx(-zs, S, w);
+        w = fmx(-zo, Sp, w);
+      }
+      if (l > 0) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) w = fmx(-Ll[e], __shfl_sync(FULL, wprev, g + e), w);
+      }
+      wbuf[row + lane] = w;
+      wprev = w;
     }
-    if (bcopy) bcopy[row + lane] = bl;
-    T w = bl;
-    if (!FROM_ZERO) {
-      const T S = nbr_dot(n, vl);
-      const T Sp = __shfl_xor_sync(FULL, S, 1);
-      w = fmx(-zs, S, w);
-      w = fmx(-zo, Sp, w);
-    }
-    if (l > 0) {
-#pragma unroll
-      for (int e = 0; e < 6; ++e) w = fmx(-Ll[e], __shfl_sync(FULL, wprev, g + e), w);
-    }
-    wbuf[row + lane] = w;
-    wprev = w;
   }
-  // backward: x_l = omega Dt_l^-1 w_l - L_(l+1)^T x_(l+1)
-  const size_t rlast = tile0 + (size_t)(nz - 1) * 32;
-  T wq = wprev, uq = FROM_ZERO ? T(0) : u[rlast + lane], Dq[6], Bq[6];
-#pragma unroll
-  for (int e = 0; e < 6; ++e) {
-    Dq[e] = A.Di[rlast * 6 + e * 32 + lane];
-    Bq[e] = T(0);
-  }
-  T xnext = T(0);
-  for (int l = nz - 1; l >= 0; --l) {
+  // backward: x_l = omega Dt_l^-1 w_l - L_(l+1)^T x_(l+1); slot d holds layer nz - 1 - (k0 + d)
+  T wq[PF], uq[PF], Dq[PF][6], Bq[PF][6];
+  auto load_b = [&](int d, int l) {
     const size_t row = tile0 + (size_t)l * 32;
-    const T wl = wq, ul = uq;
-    T Dl[6], Bl[6];
+    wq[d] = wbuf[row + lane];
+    uq[d] = FROM_ZERO ? T(0) : u[row + lane];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
-      Dl[e] = Dq[e];
-      Bl[e] = Bq[e];
+      Dq[d][e] = A.Di[row * 6 + e * 32 + lane];
+      Bq[d][e] = l < nz - 1 ? A.Lb[row * 6 + e * 32 + lane] : T(0);
     }
-    if (l > 0) {   // prefetch layer l - 1
-      const size_t rp = row - 32;
-      wq = wbuf[rp + lane];
-      if (!FROM_ZERO) uq = u[rp + lane];
+  };
+  __syncwarp();   // the forward results of this warp are read back by the same lanes; order the accesses
+#pragma unroll
+  for (int d = 0; d < PF; ++d)
+    if (d < nz) load_b(d, nz - 1 - d);
+  T xnext = T(0);
+  for (int k0 = 0; k0 < nz; k0 += PF) {
+#pragma unroll
+    for (int d = 0; d < PF; ++d) {
+      const int k = k0 + d;
+      if (k >= nz) break;   // warp-uniform
+      const int l = nz - 1 - k;
+      const size_t row = tile0 + (size_t)l * 32;
+      const T wl = wq[d], ul = uq[d];
+      T Dl[6], Bl[6];
 #pragma unroll
       for (int e = 0; e < 6; ++e) {
-        Dq[e] = A.Di[rp * 6 + e * 32 + lane];
-        Bq[e] = A.Lb[rp * 6 + e * 32 + lane];
+        Dl[e] = Dq[d][e];
+        Bl[e] = Bq[d][e];
       }
-    }
-    T x = T(0);
+      if (k + PF < nz) load_b(d, l - PF);
+      T x = T(0);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) x = fmx(Dl[e], __shfl_sync(FULL, wl, g + e), x);
-    if (l < nz - 1) {
+      for (int e = 0; e < 6; ++e) x = fmx(Dl[e], __shfl_sync(FULL, wl, g + e), x);
+      if (l < nz - 1) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) x = fmx(-Bl[e], __shfl_sync(FULL, xnext, g + e), x);
+        for (int e = 0; e < 6; ++e) x = fmx(-Bl[e], __shfl_sync(FULL, xnext, g + e), x);
+      }
+      T out = x;
+      if (!FROM_ZERO) out = fmx(T(1) - omega, ul, x);
+      uo[row + lane] = lane < 30 ? TO(out) : TO(0);
+      xnext = x;
     }
-    T out = x;
-    if (!FROM_ZERO) out = fmx(T(1) - omega, ul, x);
-    uo[row + lane] = lane < 30 ? TO(out) : TO(0);
-    xnext = x;
   }
 }
 
@@ -213,25 +233,47 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __res
   load_nbr(A, t, lane, n);
   T xm = l0 > 0 ? x[tile0 + (size_t)(l0 - 1) * 32 + lane] : T(0);
   T x0 = x[tile0 + (size_t)l0 * 32 + lane];
-  for (int l = l0; l < l1; ++l) {
+  // operands of the next layer are loaded while the current one is computed
+  T xq, vq[3][3], Aq[6], Sq[6], Uq[6];
+  auto load_op = [&](int l) {
     const size_t row = tile0 + (size_t)l * 32;
     const size_t crow = row * 6;
-    const T xp = l + 1 < nz ? x[row + 32 + lane] : T(0);
-    T v[3][3];
-    load_nbr_x(n, x, l, v);
+    xq = l + 1 < nz ? x[row + 32 + lane] : T(0);
+    load_nbr_x(n, x, l, vq);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      Aq[e] = A.Ad[crow + e * 32 + lane];
+      Sq[e] = l > 0 ? A.Cs[crow + e * 32 + lane] : T(0);
+      Uq[e] = l + 1 < nz ? A.Cu[crow + e * 32 + lane] : T(0);
+    }
+  };
+  load_op(l0);
+  for (int l = l0; l < l1; ++l) {
+    const size_t row = tile0 + (size_t)l * 32;
+    const T xp = xq;
+    T v[3][3], Al[6], Sl[6], Ul[6];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q / 3][q % 3] = vq[q / 3][q % 3];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      Al[e] = Aq[e];
+      Sl[e] = Sq[e];
+      Ul[e] = Uq[e];
+    }
+    if (l + 1 < l1) load_op(l + 1);
     const T S = nbr_dot(n, v);
     const T Sp = __shfl_xor_sync(FULL, S, 1);
     T acc = T(Z_SELF) * S;
     acc = fmx(T(Z_OTHER), Sp, acc);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) acc = fmx(A.Ad[crow + e * 32 + lane], __shfl_sync(FULL, x0, g + e), acc);
+    for (int e = 0; e < 6; ++e) acc = fmx(Al[e], __shfl_sync(FULL, x0, g + e), acc);
     if (l > 0) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc = fmx(A.Cs[crow + e * 32 + lane], __shfl_sync(FULL, xm, g + e), acc);
+      for (int e = 0; e < 6; ++e) acc = fmx(Sl[e], __shfl_sync(FULL, xm, g + e), acc);
     }
     if (l + 1 < nz) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc = fmx(A.Cu[crow + e * 32 + lane], __shfl_sync(FULL, xp, g + e), acc);
+      for (int e = 0; e < 6; ++e) acc = fmx(Ul[e], __shfl_sync(FULL, xp, g + e), acc);
     }
     if (RESID) {
       const T r = lane < 30 ? b[row + lane] - acc : T(0);
