@@ -16,6 +16,7 @@
 // copies of the coefficients, FP32 work vectors), where the FP32 pipe leaves
 // them bound by memory.
 #include <stdexcept>
+#include <string>
 
 #include "hmg_internal.h"
 
@@ -103,11 +104,12 @@ __device__ __forceinline__ T nbr_dot(const Nbr<T>& n, const T (&v)[3][3]) {
 // coefficients and u; TB: b (converted to T, and copied to bcopy when given);
 // TO: uo.  The warp walks its layers as a serial recurrence, so the operands
 // of the next PF layers are kept in flight in registers (staged slots
-// refilled as they are consumed): PF = 1 in FP64, where the FP64 pipe bounds
-// the kernel, PF = 4 in FP32, where memory latency does.
+// refilled as they are consumed).  PF = 1: four layers in flight measured
+// slower in FP32 (96.8 against 90.3 us at r4x64) and the FP64 pipe bounds the
+// FP64 kernel.
 template <typename T>
 struct SweepPF {
-  static constexpr int value = sizeof(T) == 4 ? 4 : 1;
+  static constexpr int value = 1;
 };
 
 template <typename T, bool FROM_ZERO, typename TB, typename TO>
@@ -213,6 +215,151 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_sweep(NloArgs<T> A, const TB* _
   }
 }
 
+// ---- FP32 sweep with the operands staged in shared memory.  In FP32 the
+// column recurrence is bound by memory latency, not arithmetic: the warp
+// keeps RING layers of operands in flight in a per-warp ring of shared-memory
+// slots filled by cp.async (one commit group per layer; cp.async.wait_group
+// leaves RING - 1 groups pending, so the oldest layer has arrived).  Waits
+// are the hardware's; nothing spins.
+constexpr int RING = 8;
+
+struct FwdSlot {              // forward operands of one layer
+  float L[6][32];             // L_l rows
+  float nbv[9][32];           // neighbour values u_k[j', m] of each lane
+  double b[32];               // b row (FP32 b uses the first half)
+};
+struct BwdSlot {              // backward operands of one layer
+  float D[6][32];             // omega Dt_l^-1 rows
+  float B[6][32];             // L_(l+1)^T rows
+  float w[32];
+  float u[32];
+};
+union RingSlot {
+  FwdSlot f;
+  BwdSlot b;
+};
+
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// copy `bytes` (a multiple of 16) from gmem to smem with the warp's lanes
+__device__ __forceinline__ void cpa_row(void* smem, const void* gmem, int bytes, int lane) {
+  for (int off = lane * 16; off < bytes; off += 32 * 16)
+    cpa16(static_cast<char*>(smem) + off, static_cast<const char*>(gmem) + off);
+}
+
+template <bool FROM_ZERO, typename TB, typename TO>
+__global__ void __launch_bounds__(NW * 32) k_nlo_sweep_staged(NloArgs<float> A, const TB* __restrict__ b,
+                                                              float* __restrict__ bcopy, const float* __restrict__ u,
+                                                              TO* __restrict__ uo, float* __restrict__ wbuf,
+                                                              float omega) {
+  extern __shared__ __align__(16) unsigned char nlo_smem[];
+  RingSlot* ring = reinterpret_cast<RingSlot*>(nlo_smem) + (threadIdx.x >> 5) * RING;
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * NW + (threadIdx.x >> 5);
+  if (t >= A.nt) return;   // warp-uniform; no block-wide barrier below
+  const int g = group_base(lane);
+  const int nz = A.nz;
+  const size_t tile0 = (size_t)t * nz * 32;
+  const float zs = float(Z_SELF), zo = float(Z_OTHER);
+  Nbr<float> n;
+  if (!FROM_ZERO) load_nbr(A, t, lane, n);
+
+  auto issue_f = [&](int l) {   // forward operands of layer l into slot l % RING
+    if (l < nz) {
+      FwdSlot& S = ring[l % RING].f;
+      const size_t row = tile0 + (size_t)l * 32;
+      cpa_row(S.L, A.Lf + row * 6, 6 * 32 * 4, lane);
+      cpa_row(S.b, b + row, 32 * (int)sizeof(TB), lane);
+      if (!FROM_ZERO) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) cpa4(&S.nbv[3 * k + jj][lane], u + n.base[k] + (size_t)l * 32 + 2 * jj);
+      }
+    }
+    cpa_commit();
+  };
+#pragma unroll
+  for (int l = 0; l < RING; ++l) issue_f(l);
+  float wprev = 0.f;
+  for (int l = 0; l < nz; ++l) {
+    cpa_wait<RING - 1>();
+    __syncwarp();
+    const FwdSlot& S = ring[l % RING].f;
+    const float bl = float(reinterpret_cast<const TB*>(S.b)[lane]);
+    if (bcopy) bcopy[tile0 + (size_t)l * 32 + lane] = bl;
+    float w = bl;
+    if (!FROM_ZERO) {
+      float v[3][3];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q / 3][q % 3] = S.nbv[q][lane];
+      const float Sm = nbr_dot(n, v);
+      const float Sp = __shfl_xor_sync(FULL, Sm, 1);
+      w = fmx(-zs, Sm, w);
+      w = fmx(-zo, Sp, w);
+    }
+    if (l > 0) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) w = fmx(-S.L[e][lane], __shfl_sync(FULL, wprev, g + e), w);
+    }
+    wbuf[tile0 + (size_t)l * 32 + lane] = w;
+    wprev = w;
+    __syncwarp();          // every lane is done with the slot before it is refilled
+    issue_f(l + RING);
+  }
+  cpa_wait<0>();
+  __syncwarp();            // the forward results are in memory before the backward copies read them
+
+  auto issue_b = [&](int k) {   // backward operands of step k (layer nz - 1 - k) into slot k % RING
+    if (k < nz) {
+      BwdSlot& S = ring[k % RING].b;
+      const int l = nz - 1 - k;
+      const size_t row = tile0 + (size_t)l * 32;
+      cpa_row(S.D, A.Di + row * 6, 6 * 32 * 4, lane);
+      cpa_row(S.B, A.Lb + row * 6, 6 * 32 * 4, lane);
+      cpa_row(S.w, wbuf + row, 32 * 4, lane);
+      if (!FROM_ZERO) cpa_row(S.u, u + row, 32 * 4, lane);
+    }
+    cpa_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < RING; ++k) issue_b(k);
+  float xnext = 0.f;
+  for (int k = 0; k < nz; ++k) {
+    cpa_wait<RING - 1>();
+    __syncwarp();
+    const BwdSlot& S = ring[k % RING].b;
+    const int l = nz - 1 - k;
+    const float wl = S.w[lane];
+    float x = 0.f;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) x = fmx(S.D[e][lane], __shfl_sync(FULL, wl, g + e), x);
+    if (l < nz - 1) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) x = fmx(-S.B[e][lane], __shfl_sync(FULL, xnext, g + e), x);
+    }
+    float out = x;
+    if (!FROM_ZERO) out = fmx(1.f - omega, S.u[lane], x);
+    uo[tile0 + (size_t)l * 32 + lane] = lane < 30 ? TO(out) : TO(0);
+    xnext = x;
+    __syncwarp();
+    issue_b(k + RING);
+  }
+  cpa_wait<0>();
+}
+
+constexpr size_t STAGED_SMEM = sizeof(RingSlot) * RING * NW;
+
 constexpr int LCH = 8;   // layers per warp in the layer-parallel kernels
 
 // RESID: bc[(c, l)] = sum over the cell's six unknowns of (b - H^ x);
@@ -233,7 +380,6 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __res
   load_nbr(A, t, lane, n);
   T xm = l0 > 0 ? x[tile0 + (size_t)(l0 - 1) * 32 + lane] : T(0);
   T x0 = x[tile0 + (size_t)l0 * 32 + lane];
-  // operands of the next layer are loaded while the current one is computed
   T xq, vq[3][3], Aq[6], Sq[6], Uq[6];
   auto load_op = [&](int l) {
     const size_t row = tile0 + (size_t)l * 32;
@@ -247,9 +393,13 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __res
       Uq[e] = l + 1 < nz ? A.Cu[crow + e * 32 + lane] : T(0);
     }
   };
-  load_op(l0);
+  // FP32 loads the next layer ahead (residual 75 -> 42 us at r4x64); in FP64,
+  // bound by the FP64 pipe, the lookahead measured slower (140 -> 150 us)
+  constexpr bool AHEAD = sizeof(T) == 4;
+  if (AHEAD) load_op(l0);
   for (int l = l0; l < l1; ++l) {
     const size_t row = tile0 + (size_t)l * 32;
+    if (!AHEAD) load_op(l);
     const T xp = xq;
     T v[3][3], Al[6], Sl[6], Ul[6];
 #pragma unroll
@@ -260,7 +410,7 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __res
       Sl[e] = Sq[e];
       Ul[e] = Uq[e];
     }
-    if (l + 1 < l1) load_op(l + 1);
+    if (AHEAD && l + 1 < l1) load_op(l + 1);
     const T S = nbr_dot(n, v);
     const T Sp = __shfl_xor_sync(FULL, S, 1);
     T acc = T(Z_SELF) * S;
@@ -320,6 +470,10 @@ __global__ void k_nlo_layout(int64_t n, int nz, bool to_tiled, const double* __r
 
 int warps_grid(int nt) { return (nt + NW - 1) / NW; }
 
+void cuda_ok_nlo(cudaError_t e) {
+  if (e != cudaSuccess) throw std::runtime_error(std::string("NLO kernel setup: ") + cudaGetErrorString(e));
+}
+
 int elem_grid(int64_t n) { return (int)((n + 255) / 256); }
 
 }  // namespace
@@ -352,6 +506,29 @@ void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, int dt, const v
   else resid_t(X, L0, (const float*)b, (const float*)u, bc, bc_dt, s);
 }
 
+template <typename TB, typename TO>
+void sweep_staged(const NloSys& X, int nz, const TB* b, float* bcopy, const float* u, TO* uo, float* w,
+                  double omega, cudaStream_t s) {
+  static bool attr[2] = {false, false};   // per instantiation: opt in to the ring's shared memory
+  if (u) {
+    if (!attr[0]) {
+      cuda_ok_nlo(cudaFuncSetAttribute(k_nlo_sweep_staged<false, TB, TO>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGED_SMEM));
+      attr[0] = true;
+    }
+    k_nlo_sweep_staged<false, TB, TO><<<warps_grid(X.nt), NW * 32, STAGED_SMEM, s>>>(
+        args_of(X, nz, 0.f), b, bcopy, u, uo, w, float(omega));
+  } else {
+    if (!attr[1]) {
+      cuda_ok_nlo(cudaFuncSetAttribute(k_nlo_sweep_staged<true, TB, TO>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGED_SMEM));
+      attr[1] = true;
+    }
+    k_nlo_sweep_staged<true, TB, TO><<<warps_grid(X.nt), NW * 32, STAGED_SMEM, s>>>(
+        args_of(X, nz, 0.f), b, bcopy, nullptr, uo, w, float(omega));
+  }
+}
+
 template <typename T, typename TB, typename TO>
 void sweep_t(const NloSys& X, int nz, const TB* b, T* bcopy, const T* u, TO* uo, T* w, double omega,
              cudaStream_t s) {
@@ -374,13 +551,13 @@ void launch_nlo_sweep(const NloSys& X, int nz, int dt, const void* b, int b_dt, 
   if (b_dt == HMG_FP64) {
     if (u) throw std::invalid_argument("NLO FP32 sweep: an FP64 right-hand side only from zero");
     if (uo_dt == HMG_FP64)
-      sweep_t<float, double, double>(X, nz, (const double*)b, (float*)bcopy, nullptr, (double*)uo, w, omega, s);
+      sweep_staged<double, double>(X, nz, (const double*)b, (float*)bcopy, nullptr, (double*)uo, w, omega, s);
     else
-      sweep_t<float, double, float>(X, nz, (const double*)b, (float*)bcopy, nullptr, (float*)uo, w, omega, s);
+      sweep_staged<double, float>(X, nz, (const double*)b, (float*)bcopy, nullptr, (float*)uo, w, omega, s);
   } else if (uo_dt == HMG_FP64) {
-    sweep_t<float, float, double>(X, nz, (const float*)b, nullptr, (const float*)u, (double*)uo, w, omega, s);
+    sweep_staged<float, double>(X, nz, (const float*)b, nullptr, (const float*)u, (double*)uo, w, omega, s);
   } else {
-    sweep_t<float, float, float>(X, nz, (const float*)b, nullptr, (const float*)u, (float*)uo, w, omega, s);
+    sweep_staged<float, float>(X, nz, (const float*)b, nullptr, (const float*)u, (float*)uo, w, omega, s);
   }
 }
 
