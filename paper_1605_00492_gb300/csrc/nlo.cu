@@ -380,6 +380,9 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __res
   load_nbr(A, t, lane, n);
   T xm = l0 > 0 ? x[tile0 + (size_t)(l0 - 1) * 32 + lane] : T(0);
   T x0 = x[tile0 + (size_t)l0 * 32 + lane];
+  // FP32 loads the next layer ahead (residual 75 -> 42 us at r4x64); in FP64,
+  // bound by the FP64 pipe, the lookahead measured slower (140 -> 150 us)
+  constexpr bool AHEAD = sizeof(T) == 4;
   T xq, vq[3][3], Aq[6], Sq[6], Uq[6];
   auto load_op = [&](int l) {
     const size_t row = tile0 + (size_t)l * 32;
@@ -393,37 +396,55 @@ __global__ void __launch_bounds__(NW * 32) k_nlo_op(NloArgs<T> A, const T* __res
       Uq[e] = l + 1 < nz ? A.Cu[crow + e * 32 + lane] : T(0);
     }
   };
-  // FP32 loads the next layer ahead (residual 75 -> 42 us at r4x64); in FP64,
-  // bound by the FP64 pipe, the lookahead measured slower (140 -> 150 us)
-  constexpr bool AHEAD = sizeof(T) == 4;
   if (AHEAD) load_op(l0);
   for (int l = l0; l < l1; ++l) {
     const size_t row = tile0 + (size_t)l * 32;
-    if (!AHEAD) load_op(l);
-    const T xp = xq;
-    T v[3][3], Al[6], Sl[6], Ul[6];
+    const size_t crow = row * 6;
+    T acc, xp;
+    if constexpr (AHEAD) {
+      xp = xq;
+      T v[3][3], Al[6], Sl[6], Ul[6];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q / 3][q % 3] = vq[q / 3][q % 3];
+      for (int q = 0; q < 9; ++q) v[q / 3][q % 3] = vq[q / 3][q % 3];
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      Al[e] = Aq[e];
-      Sl[e] = Sq[e];
-      Ul[e] = Uq[e];
-    }
-    if (AHEAD && l + 1 < l1) load_op(l + 1);
-    const T S = nbr_dot(n, v);
-    const T Sp = __shfl_xor_sync(FULL, S, 1);
-    T acc = T(Z_SELF) * S;
-    acc = fmx(T(Z_OTHER), Sp, acc);
+      for (int e = 0; e < 6; ++e) {
+        Al[e] = Aq[e];
+        Sl[e] = Sq[e];
+        Ul[e] = Uq[e];
+      }
+      if (l + 1 < l1) load_op(l + 1);
+      const T S = nbr_dot(n, v);
+      const T Sp = __shfl_xor_sync(FULL, S, 1);
+      acc = T(Z_SELF) * S;
+      acc = fmx(T(Z_OTHER), Sp, acc);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) acc = fmx(Al[e], __shfl_sync(FULL, x0, g + e), acc);
-    if (l > 0) {
+      for (int e = 0; e < 6; ++e) acc = fmx(Al[e], __shfl_sync(FULL, x0, g + e), acc);
+      if (l > 0) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc = fmx(Sl[e], __shfl_sync(FULL, xm, g + e), acc);
-    }
-    if (l + 1 < nz) {
+        for (int e = 0; e < 6; ++e) acc = fmx(Sl[e], __shfl_sync(FULL, xm, g + e), acc);
+      }
+      if (l + 1 < nz) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc = fmx(Ul[e], __shfl_sync(FULL, xp, g + e), acc);
+        for (int e = 0; e < 6; ++e) acc = fmx(Ul[e], __shfl_sync(FULL, xp, g + e), acc);
+      }
+    } else {
+      xp = l + 1 < nz ? x[row + 32 + lane] : T(0);
+      T v[3][3];
+      load_nbr_x(n, x, l, v);
+      const T S = nbr_dot(n, v);
+      const T Sp = __shfl_xor_sync(FULL, S, 1);
+      acc = T(Z_SELF) * S;
+      acc = fmx(T(Z_OTHER), Sp, acc);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) acc = fmx(A.Ad[crow + e * 32 + lane], __shfl_sync(FULL, x0, g + e), acc);
+      if (l > 0) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) acc = fmx(A.Cs[crow + e * 32 + lane], __shfl_sync(FULL, xm, g + e), acc);
+      }
+      if (l + 1 < nz) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) acc = fmx(A.Cu[crow + e * 32 + lane], __shfl_sync(FULL, xp, g + e), acc);
+      }
     }
     if (RESID) {
       const T r = lane < 30 ? b[row + lane] - acc : T(0);
