@@ -114,7 +114,7 @@ def breakdown(refinement=6, nlayers=64, nlevels=5):
     return out
 
 
-def nlo(cfls=(2, 8, 32), refinement=4, nlayers=64, nlevels=4):
+def nlo(cfls=(2, 8, 32), refinement=4, nlayers=64, nlevels=4, precision="fp64"):
     h = hmg.Hierarchy(refinement, nlayers, nlevels)
     b = torch.tensor(gi.nlo_rhs(6 * gi.ncells(refinement, nlayers)), device=DEV)
     out = {"cfl": []}
@@ -122,7 +122,7 @@ def nlo(cfls=(2, 8, 32), refinement=4, nlayers=64, nlevels=4):
         h.assemble(nu_cfl=cfl)
         row = {"nu_cfl": cfl}
         for name, levels in (("multigrid", 0), ("single_level", 1)):
-            kw = dict(rtol=1e-5, restart=30, levels=levels, max_iter=3000)
+            kw = dict(rtol=1e-5, restart=30, levels=levels, max_iter=3000, precision=precision)
             h.nlo_solve(b, raise_on_failure=False, **kw)
             torch.cuda.synchronize()
             _, info = h.nlo_solve(b, raise_on_failure=False, **kw)
@@ -130,9 +130,9 @@ def nlo(cfls=(2, 8, 32), refinement=4, nlayers=64, nlevels=4):
                          "converged": info["converged"]}
         out["cfl"].append(row)
     h.assemble()
-    h.nlo_solve(b, rtol=1e-5)
+    h.nlo_solve(b, rtol=1e-5, precision=precision)
     h.profile_start()
-    _, info = h.nlo_solve(b, rtol=1e-5)
+    _, info = h.nlo_solve(b, rtol=1e-5, precision=precision)
     rec = h.profile_stop()
     out["breakdown"] = {"iterations": info["iterations"],
                         "kernels": {f"{k}@{lev}": {"launches": n, "ms": round(ms, 4)}
@@ -146,6 +146,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="smaller shells (refinement 5) and fewer Courant numbers")
     ap.add_argument("--only", choices=["grid", "cfl", "history", "breakdown", "nlo"], default=None,
                     help="run one experiment")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="form of the V-cycle in the NLO experiment")
     args = ap.parse_args()
     if not torch.cuda.is_available():
         raise SystemExit("a CUDA device is required")
@@ -155,7 +157,7 @@ def main():
         "cfl": lambda: cfl_sweep([2, 8, 32] if args.quick else [2, 4, 8, 16, 32, 64], refinement=r),
         "history": lambda: history(refinement=r),
         "breakdown": lambda: breakdown(refinement=r),
-        "nlo": lambda: nlo((8,) if args.quick else (2, 8, 32)),
+        "nlo": lambda: nlo((8,) if args.quick else (2, 8, 32), precision=args.precision),
     }
     res = {k: f() for k, f in runs.items() if args.only in (None, k)}
     print(json.dumps(res))
