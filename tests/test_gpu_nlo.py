@@ -164,3 +164,29 @@ def test_nlo_reassembly_refreshes_coefficients():
     prm = helmholtz.Params(refinement=2, nlayers=4, nu_cfl=16.0)
     H16 = nlo.assemble_nlo(c.ms[0], prm).H
     assert rel_l2(c.oracle_order(c.h.nlo_apply(c.gpu(x))), H16 @ x) < 1e-13
+
+
+@pytest.mark.parametrize("r,nz,L", [(0, 2, 1), (1, 128, 2)])
+def test_nlo_edge_sizes(r, nz, L):
+    """r0 (20 columns: four tiles, one CTA; the lowest-order level below has
+    padding columns) with two layers, and 128-layer columns: operator,
+    FP64 V-cycle and mixed V-cycle against the oracle."""
+    c = case(r, nz, L)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(c.nop.n)
+    assert rel_l2(c.oracle_order(c.h.nlo_apply(c.gpu(x))), c.nop.H @ x) < 1e-13
+    b = gi.nlo_rhs(c.nop.n)
+    z_ref = nlo.vcycle(c.nop, c.lo, b)
+    assert rel_l2(c.oracle_order(c.h.nlo_vcycle(c.gpu(b))), z_ref) < 1e-11
+    assert rel_l2(c.oracle_order(c.h.nlo_vcycle(c.gpu(b), precision="mixed")), z_ref) < 1e-4
+
+
+def test_nlo_single_layer_single_level():
+    """One layer per column (no vertical coupling inside the column solve):
+    the operator and the NLO smoother alone against the oracle."""
+    c = case(0, 1, 1)
+    x = np.random.default_rng(10).standard_normal(c.nop.n)
+    assert rel_l2(c.oracle_order(c.h.nlo_apply(c.gpu(x))), c.nop.H @ x) < 1e-13
+    b = gi.nlo_rhs(c.nop.n)
+    ref = nlo.smooth(c.nop, nlo.smooth(c.nop, np.zeros(c.nop.n), b, 0.8), b, 0.8)
+    assert rel_l2(c.oracle_order(c.h.nlo_vcycle(c.gpu(b), levels=1)), ref) < 1e-11
