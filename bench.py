@@ -288,6 +288,11 @@ def cpu_baseline_subprocess(workload, iterations):
 NLO_SWEEP_BYTES_PER_CELL = 3 * 36 * 8 + 5 * 6 * 8
 NLO_SWEEP_FLOPS_PER_CELL = 2 * (66 + 36 + 72 + 6)
 NLO_SWEEP_BYTES_PER_CELL_FP32 = 3 * 36 * 4 + 5 * 6 * 4
+# DRAM bytes per launch of the general NLO sweep at r4x64 (ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum, experiments --only nlo --quick):
+# 358.4 + 30.3 MB in FP64, 176.5 + 11.8 MB in FP32 (staged)
+TRAFFIC_NLO_SWEEP_R4X64 = 388.7e6
+TRAFFIC_NLO_SWEEP_FP32_R4X64 = 188.4e6
 
 
 def nlo_section(args, world, dev, stream, hbm):
@@ -340,14 +345,16 @@ def nlo_section(args, world, dev, stream, hbm):
     out["sweep_roofline_fp32"] = {"bound": "hbm", "achieved": round(gbs32, 1), "peak": hbm, "unit": "GB/s",
                                   "frac": round(gbs32 / hbm, 4), "launches": c32, "avg_us": round(ms32 * 1e3, 2),
                                   "bytes_per_launch": NLO_SWEEP_BYTES_PER_CELL_FP32 * ncells,
-                                  "kernel": "nlo_sweep FP32 (mixed form, operands staged through shared memory)"}
+                                  "kernel": "nlo_sweep FP32 (mixed form, operands staged through shared memory)",
+                                  "traffic": TRAFFIC_NLO_SWEEP_FP32_R4X64}
     out["sweep_roofline"] = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                              "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                              "hbm_achieved_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
                              "kernel": "nlo_sweep (general sweep, 3 of the 4 per V-cycle)",
                              "launches": cnt, "avg_us": round(avg_ms * 1e3, 2),
                              "bytes_per_launch": NLO_SWEEP_BYTES_PER_CELL * ncells,
-                             "flops_per_launch": NLO_SWEEP_FLOPS_PER_CELL * ncells}
+                             "flops_per_launch": NLO_SWEEP_FLOPS_PER_CELL * ncells,
+                             "traffic": TRAFFIC_NLO_SWEEP_R4X64}
     h.close()
     return out
 

@@ -530,20 +530,24 @@ void launch_nlo_resid_restrict(const NloSys& X, const Level& L0, int dt, const v
 template <typename TB, typename TO>
 void sweep_staged(const NloSys& X, int nz, const TB* b, float* bcopy, const float* u, TO* uo, float* w,
                   double omega, cudaStream_t s) {
-  static bool attr[2] = {false, false};   // per instantiation: opt in to the ring's shared memory
+  // opt in to the ring's shared memory, once per instantiation and device
+  static unsigned long long done[2] = {0ull, 0ull};
+  int dev = 0;
+  cuda_ok_nlo(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
   if (u) {
-    if (!attr[0]) {
+    if (!(done[0] & bit)) {
       cuda_ok_nlo(cudaFuncSetAttribute(k_nlo_sweep_staged<false, TB, TO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGED_SMEM));
-      attr[0] = true;
+      done[0] |= bit;
     }
     k_nlo_sweep_staged<false, TB, TO><<<warps_grid(X.nt), NW * 32, STAGED_SMEM, s>>>(
         args_of(X, nz, 0.f), b, bcopy, u, uo, w, float(omega));
   } else {
-    if (!attr[1]) {
+    if (!(done[1] & bit)) {
       cuda_ok_nlo(cudaFuncSetAttribute(k_nlo_sweep_staged<true, TB, TO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGED_SMEM));
-      attr[1] = true;
+      done[1] |= bit;
     }
     k_nlo_sweep_staged<true, TB, TO><<<warps_grid(X.nt), NW * 32, STAGED_SMEM, s>>>(
         args_of(X, nz, 0.f), b, bcopy, nullptr, uo, w, float(omega));
