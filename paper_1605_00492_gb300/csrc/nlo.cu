@@ -15,6 +15,7 @@
 // bounds the kernels.  The mixed form runs the same kernels in FP32 (FP32
 // copies of the coefficients, FP32 work vectors), where the FP32 pipe leaves
 // them bound by memory.
+#include <atomic>
 #include <stdexcept>
 #include <string>
 
@@ -531,12 +532,12 @@ template <typename TB, typename TO>
 void sweep_staged(const NloSys& X, int nz, const TB* b, float* bcopy, const float* u, TO* uo, float* w,
                   double omega, cudaStream_t s) {
   // opt in to the ring's shared memory, once per instantiation and device
-  static unsigned long long done[2] = {0ull, 0ull};
+  static std::atomic<unsigned long long> done[2];
   int dev = 0;
   cuda_ok_nlo(cudaGetDevice(&dev));
   const unsigned long long bit = 1ull << (dev & 63);
   if (u) {
-    if (!(done[0] & bit)) {
+    if (!(done[0].load() & bit)) {
       cuda_ok_nlo(cudaFuncSetAttribute(k_nlo_sweep_staged<false, TB, TO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGED_SMEM));
       done[0] |= bit;
@@ -544,7 +545,7 @@ void sweep_staged(const NloSys& X, int nz, const TB* b, float* bcopy, const floa
     k_nlo_sweep_staged<false, TB, TO><<<warps_grid(X.nt), NW * 32, STAGED_SMEM, s>>>(
         args_of(X, nz, 0.f), b, bcopy, u, uo, w, float(omega));
   } else {
-    if (!(done[1] & bit)) {
+    if (!(done[1].load() & bit)) {
       cuda_ok_nlo(cudaFuncSetAttribute(k_nlo_sweep_staged<true, TB, TO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGED_SMEM));
       done[1] |= bit;
