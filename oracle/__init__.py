@@ -24,6 +24,9 @@ atmospheric modelling"):
 * ``nlo``       the next-to-lowest-order (BDFM1 x DG1 / DG1 x DG1) lumped
                 operator, its column block solve, the p-coarsening DG1 ->
                 DG0 and its V-cycle over the lowest-order hierarchy.
+* ``nlo_mixed`` the next-to-lowest-order velocity-pressure system (full
+                BDFM1 x DG1 and DG1 x P2 velocity masses) and its
+                Schur-complement preconditioner with the NLO V-cycle.
 * ``adjoint``   the gradient of a least-squares loss of the solution with
                 respect to the right-hand side and a per-cell coefficient of
                 the vertical coupling.
