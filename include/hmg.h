@@ -272,6 +272,43 @@ hmg_status hmg_nlo_vcycle(hmg_ctx* ctx, int precision, const double* r, double* 
 hmg_status hmg_nlo_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_params* params,
                          hmg_solve_info* info, void* stream);
 
+/* ---- NLO velocity-pressure system: Eq. (PressureVelocitySystem) with the NLO
+ * spaces above, full (consistent) velocity masses of BDFM1(T) x DG1(z) and
+ * DG1(T) x P2(z), the divergence pairings of H^ and the DG1 pressure mass,
+ * assembled on the host as CSR by the first call after each assembly.  NLO
+ * mixed COLUMN layout, in this order: horizontal edge velocity
+ * ((E nlayers + l) 2 + q) 2 + b (edge E of hmg_export_edges, points q = 0, 1
+ * at 1/3 and 2/3 along local edge k of its first column t with t's outward
+ * normal, b = bottom / top DG1 node of the layer); interior horizontal
+ * velocity ((c nlayers + l) 3 + k) 2 + b (the Whitney moment of local edge
+ * k); vertical velocity (c 3 + i) (2 nlayers - 1) + n - 1 (vertex i, P2 node
+ * n = 1 .. 2 nlayers - 1 counted from the bottom); pressure in the NLO COLUMN
+ * layout. */
+
+/* Block lengths of an NLO velocity-pressure vector.  Errors: INVALID_ARG. */
+hmg_status hmg_nlo_mixed_sizes(const hmg_ctx* ctx, int64_t* n_hedge, int64_t* n_hint, int64_t* n_vert,
+                               int64_t* n_p);
+
+/* Host-only assembly of the NLO velocity-pressure matrix A on the finest
+ * mesh of `mesh` (no context, no GPU): *n and *nnz always; the CSR arrays
+ * ptr (n + 1 int64), col (nnz int32, ascending in each row), val (nnz
+ * doubles) and the edge list (3 ncols / 2 x 4 int32, as hmg_export_edges)
+ * when non-NULL.  refinement <= 5.  Errors: INVALID_ARG. */
+hmg_status hmg_nlo_mixed_host_csr(const hmg_mesh_params* mesh, const hmg_op_params* op, int64_t* n, int64_t* nnz,
+                                  int64_t* ptr, int32_t* col, double* val, int32_t* edges);
+
+/* y = A x for FP64 device vectors in the NLO mixed COLUMN layout (x != y).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+hmg_status hmg_nlo_mixed_apply(hmg_ctx* ctx, const double* x, double* y, void* stream);
+
+/* Solve A x = b (NLO mixed COLUMN layout) with restarted flexible
+ * GMRES(params->restart) from x = 0, preconditioned on the right by Eq.
+ * (SchurComplement) with the lumped velocity-mass inverse and one NLO
+ * V-cycle (params as for hmg_nlo_vcycle) for H^^-1.  params->krylov is
+ * ignored.  Status and info as hmg_solve. */
+hmg_status hmg_nlo_mixed_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_params* params,
+                               hmg_solve_info* info, void* stream);
+
 /* Adjoint face contraction: grad_theta_K = -lambda^T (dH^/dtheta_K) p for the
  * theta given to the last hmg_assemble_helmholtz (all ones if NULL).  Only
  * the vertical term of Eq. (Preconditioner) depends on theta, through the two

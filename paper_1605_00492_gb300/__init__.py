@@ -101,6 +101,12 @@ _SIGNATURES = {
     "hmg_nlo_apply": [_P, _P, _P, _P],
     "hmg_nlo_vcycle": [_P, _I, _P, _P, _I, _I, _I, _I, _P],
     "hmg_nlo_solve": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
+    "hmg_nlo_mixed_sizes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "hmg_nlo_mixed_host_csr": [ctypes.POINTER(MeshParams), ctypes.POINTER(OpParams), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P],
+    "hmg_nlo_mixed_apply": [_P, _P, _P, _P],
+    "hmg_nlo_mixed_solve": [_P, _P, _P, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), _P],
     "hmg_to_layout": [_P, _I, _I, _P, _I, _P, _P],
     "hmg_sync": [_P, _P],
     "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
@@ -351,6 +357,37 @@ class Hierarchy:
             self._check(st)
         return x, d
 
+    # ---- next-to-lowest-order velocity-pressure system
+
+    def nlo_mixed_sizes(self):
+        """(horizontal edge, horizontal interior, vertical, pressure) block lengths."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        self._check(self.lib.hmg_nlo_mixed_sizes(self._ctx, *(ctypes.byref(x) for x in v)))
+        return tuple(x.value for x in v)
+
+    def nlo_mixed_apply(self, x, out=None, stream=None):
+        """y = A x, NLO mixed COLUMN layout, FP64 device tensors."""
+        y = out if out is not None else torch.empty_like(x)
+        self._check(self.lib.hmg_nlo_mixed_apply(self._ctx, _ptr(x.contiguous()), _ptr(y), _stream(stream)))
+        return y
+
+    def nlo_mixed_solve(self, b, out=None, stream=None, raise_on_failure=True, **kw):
+        """x = A^-1 b by GMRES(restart) with the Schur-complement preconditioner
+        and the NLO V-cycle; keyword arguments as solve (rtol defaults to the
+        paper's 1e-5).  Returns (x, info dict)."""
+        kw.setdefault("rtol", 1e-5)
+        kw.setdefault("krylov", "gmres")
+        x = out if out is not None else torch.empty_like(b)
+        info = SolveInfo()
+        prm = self.solve_params(**kw)
+        st = self.lib.hmg_nlo_mixed_solve(self._ctx, _ptr(b.contiguous()), _ptr(x), ctypes.byref(prm),
+                                          ctypes.byref(info), _stream(stream))
+        d = info.as_dict()
+        d["status"] = STATUS.get(st, st)
+        if raise_on_failure:
+            self._check(st)
+        return x, d
+
     def theta_grad(self, p, lam, out=None, stream=None):
         g = out if out is not None else torch.empty_like(p)
         self._check(self.lib.hmg_theta_grad(self._ctx, _ptr(p.contiguous()), _ptr(lam.contiguous()), _ptr(g),
@@ -405,6 +442,32 @@ def nlo_host_blocks(refinement, nlayers, c=300.0, N=0.01, nu_cfl=8.0, dx_m=0.0, 
     if st != 0:
         raise HMGError(st, lib.hmg_last_error(None).decode())
     return out
+
+
+def nlo_mixed_host_csr(refinement, nlayers, c=300.0, N=0.01, nu_cfl=8.0, dx_m=0.0, omega=0.8, radius_m=6.371e6,
+                       thickness_m=1.0e4):
+    """Host-only assembly of the NLO velocity-pressure matrix (no GPU):
+    returns (scipy CSR matrix A, edge list (ne, 4) int32)."""
+    import numpy as np
+    import scipy.sparse as sp
+    lib = load_library()
+    mp = MeshParams(refinement, nlayers, 1, radius_m, thickness_m)
+    op = OpParams(c, N, nu_cfl, dx_m, omega)
+    n, nnz = ctypes.c_int64(), ctypes.c_int64()
+    st = lib.hmg_nlo_mixed_host_csr(ctypes.byref(mp), ctypes.byref(op), ctypes.byref(n), ctypes.byref(nnz),
+                                    None, None, None, None)
+    if st != 0:
+        raise HMGError(st, lib.hmg_last_error(None).decode())
+    ptr = np.zeros(n.value + 1, dtype=np.int64)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    val = np.zeros(nnz.value)
+    edges = np.zeros((30 * 4 ** refinement, 4), dtype=np.int32)
+    st = lib.hmg_nlo_mixed_host_csr(ctypes.byref(mp), ctypes.byref(op), ctypes.byref(n), ctypes.byref(nnz),
+                                    ptr.ctypes.data_as(_P), col.ctypes.data_as(_P), val.ctypes.data_as(_P),
+                                    edges.ctypes.data_as(_P))
+    if st != 0:
+        raise HMGError(st, lib.hmg_last_error(None).decode())
+    return sp.csr_matrix((val, col, ptr), shape=(n.value, n.value)), edges
 
 
 def convert(x, dtype, stream=None):

@@ -937,6 +937,82 @@ hmg_status solve_nlo_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info
   return gmres_run(c, sys, p, info, s);
 }
 
+// ------------------------------------------------------------ NLO velocity-pressure system
+
+// Upload a host CSR matrix; the device arrays are allocated by the first
+// upload and reused afterwards (the sparsity depends on the mesh only), so
+// CUDA graphs that captured them stay valid.
+void upload_csr(hmg_ctx* c, const Csr& h, DevCsr& d) {
+  if (!d.ptr) {
+    d.nrows = h.nrows;
+    d.ncols = h.ncols;
+    d.nnz = (int64_t)h.col.size();
+    d.ptr = dalloc<int64_t>(c, h.ptr.size());
+    d.col = dalloc<int32_t>(c, h.col.size());
+    d.val = dalloc<double>(c, h.val.size());
+  }
+  require(d.nrows == h.nrows && d.nnz == (int64_t)h.col.size(), "NLO system sparsity changed");
+  cuda_ok(cudaMemcpy(d.ptr, h.ptr.data(), h.ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "upload");
+  cuda_ok(cudaMemcpy(d.col, h.col.data(), h.col.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "upload");
+  cuda_ok(cudaMemcpy(d.val, h.val.data(), h.val.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+}
+
+// The assembled system of the current assembly (host CSR assembly, one upload).
+void ensure_nlo_mixed(hmg_ctx* c) {
+  ensure_nlo(c);
+  NloMixedSys& M = c->nlomx;
+  if (M.ready) return;
+  const Level& L = c->lv[0];
+  if (c->mx.edges_host.empty()) mixed_edges_host(c, nullptr);
+  const NloMixedHost H = nlo_mixed_assemble_host(L.verts_host, L.nbr_host, c->mx.edges_host, L.nc, L.nz, c->ph);
+  M.nue = H.nue;
+  M.nui = H.nui;
+  M.nuz = H.nuz;
+  M.nu = H.nu;
+  M.np = H.np;
+  M.n = H.n;
+  upload_csr(c, H.A, M.A);
+  upload_csr(c, H.D, M.D);
+  upload_csr(c, H.Dt, M.Dt);
+  if (!M.m2inv) {
+    M.m2inv = dalloc<double>(c, M.nu);
+    for (double** v : {&M.b, &M.x, &M.t1, &M.t2}) *v = dalloc<double>(c, M.n);
+  }
+  std::vector<double> inv(H.m2diag.size());
+  for (size_t i = 0; i < inv.size(); ++i) inv[i] = 1.0 / H.m2diag[i];
+  cuda_ok(cudaMemcpy(M.m2inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+  M.ready = true;
+}
+
+// GMRES(m) on the NLO velocity-pressure system (nlomx.b, nlomx.x) with the
+// Schur-complement preconditioner; H^^-1 is one NLO V-cycle.
+hmg_status solve_nlo_mixed(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s) {
+  NloMixedSys& M = c->nlomx;
+  NloSys& X = c->nlo;
+  const int nz = c->lv[0].nz;
+  const CycleCfg cfg = nlo_cfg(c, p.nu_pre, p.nu_post, p.n_coarse, p.levels, p.precision);
+  KrylovSystem sys;
+  sys.n = M.n;
+  sys.b = M.b;
+  sys.x = M.x;
+  sys.tmp = M.t1;
+  sys.apply = [c, &M](const double* x, double* y, cudaStream_t st) {
+    LAUNCH(c, HMG_K_APPLY, 0, st, launch_csr_spmv(M.A, x, 1.0, nullptr, nullptr, y, st));
+  };
+  sys.precond = [c, &M, &X, cfg, nz](const double* r, double* z, cudaStream_t st) {
+    const double ac2 = c->ph.a * c->ph.c2;
+    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mul(M.nu, r, M.m2inv, M.t2, st));                 // M2inv r_U
+    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv(M.D, M.t2, -ac2, r + M.nu, nullptr, M.t2 + M.nu, st));
+    LAUNCH(c, HMG_K_LAYOUT, 0, st, launch_nlo_layout(X, nz, true, M.t2 + M.nu, X.t1, st));
+    nlo_cycle(c, cfg, X.t1, X.t2, st);
+    LAUNCH(c, HMG_K_LAYOUT, 0, st, launch_nlo_layout(X, nz, false, X.t2, z + M.nu, st));
+    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv(M.Dt, z + M.nu, c->ph.a, r, M.m2inv, z, st));
+  };
+  sys.orth = p.orth == 2 ? 2 : 1;
+  sys.key = (4LL << 60) + (sys.orth == 2 ? (1LL << 59) : 0) + graph_key(cfg, true, 0);
+  return gmres_run(c, sys, p, info, s);
+}
+
 void check_solve_params(const hmg_solve_params* p) {
   require(p != nullptr, "params is NULL");
   require(p->precision == HMG_PRECISION_FP64 || p->precision == HMG_PRECISION_MIXED, "bad precision");
@@ -1110,6 +1186,7 @@ hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const do
     cudaStream_t s = as_stream(stream);
     ctx->assembled = false;
     ctx->nlo.ready = false;
+    ctx->nlomx.ready = false;
     ctx->op = *p;
     const Phys& ph = (ctx->ph = make_phys(ctx->mp, *p));
     ctx->has_theta = theta != nullptr;
@@ -1370,6 +1447,85 @@ hmg_status hmg_nlo_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_sol
     LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, true, b, X.b, s));
     result = solve_nlo_tiled(ctx, *params, info, s);
     LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_nlo_layout(X, nz, false, X.x, x, s));
+    cuda_ok(cudaStreamSynchronize(s), "solve");
+  });
+  if (st != HMG_OK) return st;
+  if (result == HMG_ERR_NOT_CONVERGED) ctx->err = "maximum number of iterations reached";
+  if (result == HMG_ERR_BREAKDOWN) ctx->err = "GMRES breakdown";
+  if (result == HMG_ERR_NONFINITE) ctx->err = "non-finite residual";
+  return result;
+}
+
+hmg_status hmg_nlo_mixed_sizes(const hmg_ctx* ctx, int64_t* n_hedge, int64_t* n_hint, int64_t* n_vert,
+                               int64_t* n_p) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  const Level& L = ctx->lv[0];
+  const int64_t ne = (int64_t)L.nc * 3 / 2;
+  if (n_hedge) *n_hedge = ne * L.nz * 4;
+  if (n_hint) *n_hint = (int64_t)L.nc * L.nz * 6;
+  if (n_vert) *n_vert = (int64_t)L.nc * 3 * (2 * L.nz - 1);
+  if (n_p) *n_p = (int64_t)L.nc * L.nz * 6;
+  return HMG_OK;
+}
+
+hmg_status hmg_nlo_mixed_host_csr(const hmg_mesh_params* mesh, const hmg_op_params* op, int64_t* n, int64_t* nnz,
+                                  int64_t* ptr, int32_t* col, double* val, int32_t* edges) {
+  return guarded(nullptr, [&] {
+    require(mesh != nullptr, "mesh is NULL");
+    require(mesh->refinement >= 0 && mesh->refinement <= 5, "refinement must be in [0, 5]");
+    require(mesh->nlayers >= 1 && mesh->nlayers <= 256, "nlayers must be in [1, 256]");
+    require(mesh->radius_m > 0 && mesh->thickness_m > 0, "radius_m and thickness_m must be positive");
+    check_op_params(op);
+    require(n && nnz, "n and nnz must be non-NULL");
+    std::vector<HostLevel> host = build_mesh_hierarchy(mesh->refinement, 1);
+    const HostLevel& H = host[0];
+    std::vector<int32_t> el;   // edge list (t, k, tn, kn), t < tn, by t then k
+    for (int t = 0; t < H.ncols; ++t)
+      for (int k = 0; k < 3; ++k) {
+        const int tn = H.nbr[3 * t + k];
+        if (t < tn) {
+          int kn = 0;
+          while (kn < 3 && H.nbr[3 * tn + kn] != t) ++kn;
+          require(kn < 3, "mesh neighbours are not symmetric");
+          el.insert(el.end(), {t, k, tn, kn});
+        }
+      }
+    const NloMixedHost X = nlo_mixed_assemble_host(H.verts, H.nbr, el, H.ncols, mesh->nlayers, make_phys(*mesh, *op));
+    *n = X.n;
+    *nnz = (int64_t)X.A.col.size();
+    if (ptr) std::memcpy(ptr, X.A.ptr.data(), X.A.ptr.size() * sizeof(int64_t));
+    if (col) std::memcpy(col, X.A.col.data(), X.A.col.size() * sizeof(int32_t));
+    if (val) std::memcpy(val, X.A.val.data(), X.A.val.size() * sizeof(double));
+    if (edges) std::memcpy(edges, el.data(), el.size() * sizeof(int32_t));
+  });
+}
+
+hmg_status hmg_nlo_mixed_apply(hmg_ctx* ctx, const double* x, double* y, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(x && y && x != y, "x and y must be distinct non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_nlo_mixed(ctx);
+    LAUNCH(ctx, HMG_K_APPLY, 0, s, launch_csr_spmv(ctx->nlomx.A, x, 1.0, nullptr, nullptr, y, s));
+  });
+}
+
+hmg_status hmg_nlo_mixed_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_params* params,
+                               hmg_solve_info* info, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  hmg_status result = HMG_OK;
+  hmg_status st = guarded(ctx, [&] {
+    check_solve_params(params);
+    require(params->levels <= (int)ctx->lv.size() + 1, "levels must be in [0, nlevels + 1]");
+    require(b && x, "b and x must be non-NULL device pointers");
+    need_assembled(ctx);
+    cudaStream_t s = as_stream(stream);
+    ensure_nlo_mixed(ctx);
+    NloMixedSys& M = ctx->nlomx;
+    cuda_ok(cudaMemcpyAsync(M.b, b, (size_t)M.n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    result = solve_nlo_mixed(ctx, *params, info, s);
+    cuda_ok(cudaMemcpyAsync(x, M.x, (size_t)M.n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
   if (st != HMG_OK) return st;

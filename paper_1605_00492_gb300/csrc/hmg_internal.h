@@ -146,6 +146,43 @@ NloHost nlo_assemble_host(const std::vector<double>& verts, const std::vector<in
 // Dinv[cell] = omega Dt_l^-1.
 void nlo_factor_host(const NloHost& H, double omega, std::vector<double>& Lf, std::vector<double>& Dinv);
 
+// CSR matrix (host or device arrays)
+struct Csr {
+  int64_t nrows = 0, ncols = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+};
+// The NLO velocity-pressure system on the host: A (n x n), D (np x nu),
+// D^T (nu x np) and the diagonal of M2~ (nu), in the NLO mixed COLUMN layout.
+struct NloMixedHost {
+  int64_t nue = 0, nui = 0, nuz = 0, nu = 0, np = 0, n = 0;
+  Csr A, D, Dt;
+  std::vector<double> m2diag;
+};
+NloMixedHost nlo_mixed_assemble_host(const std::vector<double>& verts, const std::vector<int32_t>& nbr,
+                                     const std::vector<int32_t>& edges, int nc, int nz, const Phys& ph);
+
+// A CSR matrix on the device.
+struct DevCsr {
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int64_t* ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+// y = (y0 + alpha A x) * s, elementwise s and y0 optional (nlo_mixed.cu)
+void launch_csr_spmv(const DevCsr& A, const double* x, double alpha, const double* y0, const double* s, double* y,
+                     cudaStream_t st);
+void launch_mul(int64_t n, const double* a, const double* b, double* y, cudaStream_t st);   // y = a * b
+// The NLO velocity-pressure system on the device (NLO mixed COLUMN layout).
+struct NloMixedSys {
+  bool ready = false;
+  int64_t nue = 0, nui = 0, nuz = 0, nu = 0, np = 0, n = 0;
+  DevCsr A, D, Dt;
+  double* m2inv = nullptr;                                      // nu
+  double *b = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr;   // n
+};
+
 constexpr int NLO_TILE = 5;   // columns per warp: lanes 6 c5 + u, lanes 30 and 31 padding
 // The NLO system of the finest mesh.  Vectors: tiles of 5 columns, one row
 // of 32 doubles per (tile, layer), index (t * nz + l) * 32 + 6 c5 + u
@@ -322,4 +359,5 @@ struct hmg_ctx {
 
   hmg::MixedSys mx;               // velocity-pressure system, set up by its first use
   hmg::NloSys nlo;                // next-to-lowest-order system, set up by its first use
+  hmg::NloMixedSys nlomx;         // next-to-lowest-order velocity-pressure system, set up by its first use
 };

@@ -1,0 +1,59 @@
+// Kernels of the next-to-lowest-order velocity-pressure system (Eq.
+// PressureVelocitySystem at NLO): the assembled operator and the two outer
+// factors of the Schur-complement preconditioner (Eq. SchurComplement with
+// the lumped inverse of Eq. LumpedMass) are CSR products, the form in which
+// the paper's implementation holds them.  Rows have 10 to 50 entries, so
+// eight lanes share a row: each lane accumulates a strided part of the row
+// and the eight partial sums are combined by shuffles in a fixed order, so
+// the result does not depend on scheduling.
+#include "hmg_internal.h"
+
+namespace hmg {
+
+namespace {
+
+constexpr int LPR = 8;                 // lanes per row
+constexpr unsigned FULL = 0xffffffffu;
+
+// y[i] = (y0[i] + alpha * sum_j A_ij x_j) * s[i]   (y0, s optional)
+__global__ void k_csr_spmv(int64_t nrows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ x, double alpha,
+                           const double* __restrict__ y0, const double* __restrict__ s, double* __restrict__ y) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = gid / LPR;
+  const int sub = (int)(gid % LPR);
+  double acc = 0.0;
+  if (row < nrows) {
+    const int64_t p1 = ptr[row + 1];
+    for (int64_t p = ptr[row] + sub; p < p1; p += LPR) acc = fma(val[p], x[col[p]], acc);
+  }
+#pragma unroll
+  for (int off = LPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(FULL, acc, off, LPR);
+  if (row < nrows && sub == 0) {
+    double v = alpha * acc;
+    if (y0) v += y0[row];
+    if (s) v *= s[row];
+    y[row] = v;
+  }
+}
+
+__global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                      double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a[i] * b[i];
+}
+
+int grid_of(int64_t threads) { return (int)((threads + 255) / 256); }
+
+}  // namespace
+
+void launch_csr_spmv(const DevCsr& A, const double* x, double alpha, const double* y0, const double* s, double* y,
+                     cudaStream_t st) {
+  k_csr_spmv<<<grid_of(A.nrows * LPR), 256, 0, st>>>(A.nrows, A.ptr, A.col, A.val, x, alpha, y0, s, y);
+}
+
+void launch_mul(int64_t n, const double* a, const double* b, double* y, cudaStream_t st) {
+  k_mul<<<grid_of(n), 256, 0, st>>>(n, a, b, y);
+}
+
+}  // namespace hmg

@@ -23,6 +23,7 @@
 // divergence integrals int_T lam_j div v_a are the same on every triangle and
 // the energies are int_T |v_a|^2 = int_Tref v^T G v / det J with the metric
 // G = J^T J of the triangle's affine map J.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <stdexcept>
@@ -144,6 +145,7 @@ void invert(double* a, int n) {
 struct RefBDFM {
   double div[3][9];
   double Q[9][3];
+  double M[9][9][4];   // int v_a,x v_a',x ; v_a,x v_a',y ; v_a,y v_a',x ; v_a,y v_a',y
 };
 
 RefBDFM reference_bdfm() {
@@ -185,19 +187,29 @@ RefBDFM reference_bdfm() {
     bary(rule.x[p], rule.y[p], lam);
     double sv[9][2], sd[9];
     for (int f = 0; f < 9; ++f) span_eval(f, rule.x[p], rule.y[p], sv[f], &sd[f]);
+    double vx[9], vy[9];
     for (int a = 0; a < 9; ++a) {
-      double vx = 0, vy = 0, dv = 0;
+      double dv = 0;
+      vx[a] = vy[a] = 0;
       for (int f = 0; f < 9; ++f) {
-        vx += Phi[f * 9 + a] * sv[f][0];
-        vy += Phi[f * 9 + a] * sv[f][1];
+        vx[a] += Phi[f * 9 + a] * sv[f][0];
+        vy[a] += Phi[f * 9 + a] * sv[f][1];
         dv += Phi[f * 9 + a] * sd[f];
       }
       const double w = rule.w[p];
-      R.Q[a][0] += w * vx * vx;
-      R.Q[a][1] += w * vx * vy;
-      R.Q[a][2] += w * vy * vy;
+      R.Q[a][0] += w * vx[a] * vx[a];
+      R.Q[a][1] += w * vx[a] * vy[a];
+      R.Q[a][2] += w * vy[a] * vy[a];
       for (int j = 0; j < 3; ++j) R.div[j][a] += w * lam[j] * dv;
     }
+    for (int a = 0; a < 9; ++a)
+      for (int a2 = 0; a2 < 9; ++a2) {
+        const double w = rule.w[p];
+        R.M[a][a2][0] += w * vx[a] * vx[a2];
+        R.M[a][a2][1] += w * vx[a] * vy[a2];
+        R.M[a][a2][2] += w * vy[a] * vx[a2];
+        R.M[a][a2][3] += w * vy[a] * vy[a2];
+      }
   }
   return R;
 }
@@ -354,6 +366,195 @@ void nlo_factor_host(const NloHost& H, double omega, std::vector<double>& Lf, st
       Dprev = inv;
     }
   }
+}
+
+// ---- the NLO velocity-pressure system (Eq. PressureVelocitySystem at NLO)
+//
+// Unknowns (the NLO mixed COLUMN layout of hmg.h): horizontal edge velocity
+// ((E nz + l) 2 + q) 2 + b for edge E of the edge list (t, k, tn, kn), point
+// q along edge k of column t and the normal of t; interior horizontal
+// velocity ((c nz + l) 3 + k) 2 + b; vertical velocity (c 3 + i) (2 nz - 1) +
+// node - 1 (node 1 .. 2 nz - 1 of P2 in z); pressure ((c nz + l) 3 + j) 2 + m.
+// Per cell the element matrices are: the BDFM1 mass of the column (the
+// Piola-mapped reference moments and the triangle's metric) times the DG1
+// mass in z over dz; the vertical mass lam_i lam_i' / (4 |T_l|^2) times the
+// P2 mass in z; the divergence pairings (reference integrals, the same on
+// every triangle) and the DG1 pressure mass.  A is assembled as CSR from the
+// cells' triplets (counting sort by row, then sort and merge each row).
+namespace {
+
+struct Trip {
+  int32_t r, c;
+  double v;
+};
+
+void to_csr(std::vector<Trip>& t, int64_t nrows, int64_t ncols, Csr& out) {
+  out.nrows = nrows;
+  out.ncols = ncols;
+  std::vector<int64_t> cnt(nrows + 1, 0);
+  for (const Trip& x : t) ++cnt[x.r + 1];
+  for (int64_t i = 0; i < nrows; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int32_t> cs(t.size());
+  std::vector<double> vs(t.size());
+  {
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (const Trip& x : t) {
+      const int64_t p = pos[x.r]++;
+      cs[p] = x.c;
+      vs[p] = x.v;
+    }
+  }
+  std::vector<Trip>().swap(t);
+  out.ptr.assign(nrows + 1, 0);
+  out.col.clear();
+  out.val.clear();
+  out.col.reserve(cs.size() / 2);
+  out.val.reserve(cs.size() / 2);
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < nrows; ++i) {
+    row.clear();
+    for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) row.emplace_back(cs[p], vs[p]);
+    std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (size_t k = 0; k < row.size();) {
+      double v = 0.0;
+      const int32_t c = row[k].first;
+      while (k < row.size() && row[k].first == c) v += row[k++].second;
+      out.col.push_back(c);
+      out.val.push_back(v);
+    }
+    out.ptr[i + 1] = (int64_t)out.col.size();
+  }
+}
+
+}  // namespace
+
+NloMixedHost nlo_mixed_assemble_host(const std::vector<double>& verts, const std::vector<int32_t>& nbrs,
+                                     const std::vector<int32_t>& edges, int nc, int nz, const Phys& ph) {
+  const RefBDFM R = reference_bdfm();
+  const int ne = (int)(edges.size() / 4);
+  NloMixedHost X;
+  X.nue = (int64_t)ne * nz * 4;
+  X.nui = (int64_t)nc * nz * 6;
+  X.nuz = (int64_t)nc * 3 * (2 * nz - 1);
+  X.nu = X.nue + X.nui + X.nuz;
+  X.np = (int64_t)nc * nz * 6;
+  X.n = X.nu + X.np;
+  if (X.n >= (int64_t)1 << 31) throw std::runtime_error("NLO velocity-pressure system too large for 32-bit indices");
+  const double dz = ph.dz, a = ph.a, ac2 = ph.a * ph.c2, vz = 1.0 + ph.wn2;
+  auto vert = [&](int c, int k, int x) { return verts[(size_t)c * 9 + 3 * k + x]; };
+  // per column and local BDFM1 unknown: global edge-or-interior index base and sign
+  std::vector<int64_t> gbase((size_t)nc * 9);
+  std::vector<double> gsign((size_t)nc * 9, 1.0);
+  for (int c = 0; c < nc; ++c)
+    for (int k = 0; k < 3; ++k) gbase[(size_t)c * 9 + 6 + k] = -1 - k;   // interior: resolved per layer below
+  for (int e = 0; e < ne; ++e) {
+    const int t = edges[4 * e], k = edges[4 * e + 1], tn = edges[4 * e + 2], kn = edges[4 * e + 3];
+    const int i = (k + 1) % 3, in = (kn + 1) % 3, jn = (kn + 2) % 3;
+    double dsame = 0.0, drev = 0.0;
+    for (int x = 0; x < 3; ++x) {
+      dsame += std::fabs(vert(t, i, x) - vert(tn, in, x));
+      drev += std::fabs(vert(t, i, x) - vert(tn, jn, x));
+    }
+    if (!(dsame < 1e-12 || drev < 1e-12)) throw std::runtime_error("neighbour edge does not match");
+    const bool rev = drev < dsame;
+    for (int q = 0; q < 2; ++q) {
+      gbase[(size_t)t * 9 + 2 * k + q] = ((int64_t)e * nz * 2 + q) * 2;             // + l * 4 + b
+      const int qn = rev ? 1 - q : q;
+      gbase[(size_t)tn * 9 + 2 * kn + qn] = ((int64_t)e * nz * 2 + q) * 2;
+      gsign[(size_t)tn * 9 + 2 * kn + qn] = -1.0;
+    }
+  }
+  (void)nbrs;
+  const double MZ1[2][2] = {{1.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 1.0 / 3.0}};
+  const double G[2][3] = {{-5.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0}, {-1.0 / 6.0, -2.0 / 3.0, 5.0 / 6.0}};
+  const double P2[3][3] = {{4.0 / 30, 2.0 / 30, -1.0 / 30}, {2.0 / 30, 16.0 / 30, 2.0 / 30}, {-1.0 / 30, 2.0 / 30, 4.0 / 30}};
+  auto PM = [](int j, int i) { return (i == j ? 2.0 : 1.0) / 12.0; };
+  const int nzn = 2 * nz - 1;
+
+  std::vector<Trip> tA, tD, tDt;
+  tA.reserve((size_t)nc * nz * 770);
+  tD.reserve((size_t)nc * nz * 162);
+  tDt.reserve((size_t)nc * nz * 162);
+  X.m2diag.assign(X.nu, 0.0);
+  for (int c = 0; c < nc; ++c) {
+    double J0[3], J1[3];
+    for (int x = 0; x < 3; ++x) {
+      J0[x] = vert(c, 1, x) - vert(c, 0, x);
+      J1[x] = vert(c, 2, x) - vert(c, 0, x);
+    }
+    const double g00 = J0[0] * J0[0] + J0[1] * J0[1] + J0[2] * J0[2];
+    const double g01 = J0[0] * J1[0] + J0[1] * J1[1] + J0[2] * J1[2];
+    const double g11 = J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2];
+    const double det = std::sqrt(g00 * g11 - g01 * g01);
+    const double area1 = 0.5 * det;
+    double mass[9][9];
+    for (int p = 0; p < 9; ++p)
+      for (int q = 0; q < 9; ++q)
+        mass[p][q] = (g00 * R.M[p][q][0] + g01 * (R.M[p][q][1] + R.M[p][q][2]) + g11 * R.M[p][q][3]) / det;
+    for (int l = 0; l < nz; ++l) {
+      const double rho = ph.R + (l + 0.5) * dz;
+      const double At = area1 * rho * rho;
+      int64_t h[18];
+      double hs[18];
+      for (int p = 0; p < 9; ++p)
+        for (int b = 0; b < 2; ++b) {
+          const int64_t base = gbase[(size_t)c * 9 + p];
+          h[2 * p + b] = base >= 0 ? base + (int64_t)l * 4 + b : X.nue + (((int64_t)c * nz + l) * 3 + (p - 6)) * 2 + b;
+          hs[2 * p + b] = gsign[(size_t)c * 9 + p];
+        }
+      int64_t v[9];   // (i, kz): vertical unknowns of the cell, -1 on the top and bottom boundary
+      for (int i = 0; i < 3; ++i)
+        for (int kz = 0; kz < 3; ++kz) {
+          const int node = 2 * l + kz;
+          v[3 * i + kz] = (node == 0 || node == 2 * nz) ? -1 : X.nue + X.nui + ((int64_t)c * 3 + i) * nzn + node - 1;
+        }
+      int64_t pr[6];
+      for (int u = 0; u < 6; ++u) pr[u] = X.nu + ((int64_t)c * nz + l) * 6 + u;
+      // M2^h
+      for (int r1 = 0; r1 < 18; ++r1)
+        for (int r2 = 0; r2 < 18; ++r2) {
+          const double val = hs[r1] * hs[r2] * mass[r1 / 2][r2 / 2] * MZ1[r1 % 2][r2 % 2] / dz;
+          tA.push_back({(int32_t)h[r1], (int32_t)h[r2], val});
+          if (r1 == r2) X.m2diag[h[r1]] += val;
+        }
+      // (1 + w_N^2) M2^z
+      for (int r1 = 0; r1 < 9; ++r1) {
+        if (v[r1] < 0) continue;
+        for (int r2 = 0; r2 < 9; ++r2) {
+          if (v[r2] < 0) continue;
+          const double val = vz * PM(r1 / 3, r2 / 3) / (4.0 * At) * dz * P2[r1 % 3][r2 % 3];
+          tA.push_back({(int32_t)v[r1], (int32_t)v[r2], val});
+          if (r1 == r2) X.m2diag[v[r1]] += val;
+        }
+      }
+      // divergence pairings: A(p, u) = a c^2 D, A(u, p) = -a D^T
+      for (int u = 0; u < 6; ++u) {
+        const int j = u / 2, m = u % 2;
+        for (int r = 0; r < 18; ++r) {
+          const double d = hs[r] * R.div[j][r / 2] * MZ1[m][r % 2];
+          tA.push_back({(int32_t)pr[u], (int32_t)h[r], ac2 * d});
+          tA.push_back({(int32_t)h[r], (int32_t)pr[u], -a * d});
+          tD.push_back({(int32_t)(pr[u] - X.nu), (int32_t)h[r], d});
+          tDt.push_back({(int32_t)h[r], (int32_t)(pr[u] - X.nu), d});
+        }
+        for (int r = 0; r < 9; ++r) {
+          if (v[r] < 0) continue;
+          const double d = PM(j, r / 3) / 2.0 * G[m][r % 3];
+          tA.push_back({(int32_t)pr[u], (int32_t)v[r], ac2 * d});
+          tA.push_back({(int32_t)v[r], (int32_t)pr[u], -a * d});
+          tD.push_back({(int32_t)(pr[u] - X.nu), (int32_t)v[r], d});
+          tDt.push_back({(int32_t)v[r], (int32_t)(pr[u] - X.nu), d});
+        }
+        // M3
+        for (int u2 = 0; u2 < 6; ++u2)
+          tA.push_back({(int32_t)pr[u], (int32_t)pr[u2], At * dz * PM(j, u2 / 2) * MZ1[m][u2 % 2]});
+      }
+    }
+  }
+  to_csr(tA, X.n, X.n, X.A);
+  to_csr(tD, X.np, X.nu, X.D);
+  to_csr(tDt, X.nu, X.np, X.Dt);
+  return X;
 }
 
 // Repack the per-cell blocks into the NLO tile layout (NloSys).

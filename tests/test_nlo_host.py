@@ -73,3 +73,27 @@ def test_nlo_host_blocks_argument_errors(hmg):
         hmg.nlo_host_blocks(1, 0)
     with pytest.raises(hmg.HMGError):
         hmg.nlo_host_blocks(1, 3, omega=2.5)
+
+
+@pytest.mark.parametrize("r,nz", [(1, 3), (2, 2)])
+def test_nlo_mixed_host_csr_matches_oracle(hmg, r, nz):
+    """The library's host CSR of the NLO velocity-pressure matrix (element
+    matrices from the Piola-mapped reference element) against the oracle's
+    assembled A, after matching the unknowns and their signs."""
+    from oracle import nlo_mixed
+    from tests.helpers import nlo_mixed_permutation
+    A, edges = hmg.nlo_mixed_host_csr(r, nz)
+    B = hmg.nlo_host_blocks(r, nz)
+    m = mesh.hierarchy(r, 1)[0]
+    prm = helmholtz.Params(refinement=r, nlayers=nz)
+    nop = nlo.assemble_nlo(m, prm)
+    mop = nlo_mixed.assemble_nlo_mixed(m, prm, nop)
+    idx, sgn = nlo_mixed_permutation(B["verts"].mean(axis=1), B["verts"], edges, m, nz)
+    assert A.shape == mop.A.shape and len(np.unique(idx)) == A.shape[0]
+    import scipy.sparse as sp
+    S = sp.diags(sgn)
+    Ao = (S @ mop.A[idx][:, idx] @ S).tocsr()
+    D = (A - Ao).tocsr()
+    scale = np.abs(Ao).max(axis=1).toarray().ravel()
+    assert np.all(np.abs(D).max(axis=1).toarray().ravel() <= 1e-12 * scale)
+    assert A.nnz == Ao.nnz
