@@ -355,6 +355,32 @@ def nlo_section(args, world, dev, stream, hbm):
                              "bytes_per_launch": NLO_SWEEP_BYTES_PER_CELL * ncells,
                              "flops_per_launch": NLO_SWEEP_FLOPS_PER_CELL * ncells,
                              "traffic": TRAFFIC_NLO_SWEEP_R4X64}
+    # the velocity-pressure system at NLO (Table "SingleNodePerformance", NLO
+    # row: 7.9 million unknowns, GMRES to 1e-5), right-hand side (M2~ R_U, M3 R_P)
+    sizes = h.nlo_mixed_sizes()
+    ntot = sum(sizes)
+    nu = ntot - sizes[3]
+    R = torch.tensor(gi.mixed_rhs(nu, sizes[3]), dtype=torch.float64, device=dev)
+    Ru, Rp = R.clone(), R.clone()
+    Ru[nu:] = 0
+    Rp[:nu] = 0
+    bvp = torch.cat([h.nlo_mixed_apply(Ru)[:nu], h.nlo_mixed_apply(Rp)[nu:]])
+    vp = {"unknowns": int(ntot), "rtol": 1e-5,
+          "krylov": "GMRES(30), Schur-complement preconditioner, one NLO V-cycle for H^^-1"}
+    for form in ("fp64", "mixed"):
+        kw = dict(precision=form, rtol=1e-5, restart=30, max_iter=300)
+        h.nlo_mixed_solve(bvp, **kw)
+        reps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            _, info = h.nlo_mixed_solve(bvp, **kw)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / reps
+        vp[form] = {"solves_per_s": round(world / (ms / 1e3), 3), "ms_per_solve": round(ms, 4),
+                    "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"]}
+    out["velocity_pressure"] = vp
     h.close()
     return out
 

@@ -219,3 +219,43 @@ def test_nlo_full_size_properties():
     assert i64["iterations"] <= 40
     assert float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)) < 1e-6
     h.close()
+
+
+def test_nlo_velocity_pressure_system_full_size():
+    """r4x64 at NLO (Table "GridSetup": 7.9 M unknowns): the off-diagonal
+    blocks are adjoint up to the factor -c^2 (<D U, P> = <U, D^T P>), the
+    velocity mass is symmetric, and GMRES with the Schur-complement
+    preconditioner converges with both V-cycle forms to the same solution."""
+    w = gi.WORKLOADS["r4x64nlo"]
+    h = hmg.Hierarchy(w["refinement"], w["nlayers"], w["nlevels"])
+    h.assemble()
+    sizes = h.nlo_mixed_sizes()
+    n = sum(sizes)
+    nu = n - sizes[3]
+    assert round(n / 1e6, 1) == 7.9
+    g = torch.Generator(device=DEV).manual_seed(29)
+    rnd = lambda: torch.randn(n, generator=g, dtype=torch.float64, device=DEV)
+    U1, U2, P = rnd(), rnd(), rnd()
+    U1[nu:] = 0
+    U2[nu:] = 0
+    P[:nu] = 0
+    yP = h.nlo_mixed_apply(P)          # (-a D^T P, M3 P)
+    yU = h.nlo_mixed_apply(U1)         # (M2~ U1, a c^2 D U1)
+    ratio = float(torch.dot(yU[nu:], P[nu:])) / float(torch.dot(U1[:nu], yP[:nu]))
+    assert ratio == pytest.approx(-300.0 ** 2, rel=1e-10)
+    yU2 = h.nlo_mixed_apply(U2)
+    assert float(torch.dot(yU[:nu], U2[:nu])) == pytest.approx(float(torch.dot(U1[:nu], yU2[:nu])), rel=1e-12)
+    R = torch.tensor(gi.mixed_rhs(nu, sizes[3]), dtype=torch.float64, device=DEV)
+    Ru, Rp = R.clone(), R.clone()
+    Ru[nu:] = 0
+    Rp[:nu] = 0
+    b = torch.cat([h.nlo_mixed_apply(Ru)[:nu], h.nlo_mixed_apply(Rp)[nu:]])
+    x64, i64 = h.nlo_mixed_solve(b, rtol=1e-10, max_iter=500)
+    xm, im = h.nlo_mixed_solve(b, rtol=1e-10, precision="mixed", max_iter=500)
+    assert i64["converged"] == 1 and im["converged"] == 1
+    assert i64["true_rel_residual"] < 2e-10 and im["true_rel_residual"] < 2e-10
+    for sl in (slice(0, nu), slice(nu, n)):
+        assert float(torch.linalg.norm(xm[sl] - x64[sl]) / torch.linalg.norm(x64[sl])) < 1e-7
+    _, i5 = h.nlo_mixed_solve(b, rtol=1e-5)
+    assert i5["iterations"] <= 30
+    h.close()
