@@ -12,7 +12,12 @@ namespace hmg {
 
 namespace {
 
-constexpr int LPR = 8;                 // lanes per row
+// Lanes per row.  On GB300 every FP64 warp instruction costs the same
+// whatever its active lanes, and the FP64 pipe bounds this product: per row
+// it issues the FMAs, the shuffle sum (log2 LPR adds per warp) and the
+// epilogue (per warp).  Eight lanes per row made the sums and epilogues
+// dominate; four lanes keep loads coalesced over a row's consecutive entries.
+constexpr int LPR = 4;
 constexpr unsigned FULL = 0xffffffffu;
 
 // y[i] = (y0[i] + alpha * sum_j A_ij x_j) * s[i]   (y0, s optional)
@@ -32,8 +37,9 @@ __global__ void k_csr_spmv(int64_t nrows, const int64_t* __restrict__ ptr, const
 #pragma unroll
   for (int off = LPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(FULL, acc, off, LPR);
   if (row < nrows && sub == 0) {
-    double v = alpha * acc;
-    if (y0) v += y0[row];
+    double v = acc;
+    if (y0) v = fma(alpha, acc, y0[row]);
+    else if (alpha != 1.0) v = alpha * acc;
     if (s) v *= s[row];
     y[row] = v;
   }
