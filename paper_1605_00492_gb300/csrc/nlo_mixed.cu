@@ -2,10 +2,10 @@
 // PressureVelocitySystem at NLO): the assembled operator and the two outer
 // factors of the Schur-complement preconditioner (Eq. SchurComplement with
 // the lumped inverse of Eq. LumpedMass) are CSR products, the form in which
-// the paper's implementation holds them.  Rows have 10 to 50 entries, so
-// eight lanes share a row: each lane accumulates a strided part of the row
-// and the eight partial sums are combined by shuffles in a fixed order, so
-// the result does not depend on scheduling.
+// the paper's implementation holds them.  Rows have 10 to 50 entries; a few
+// lanes share a row, each accumulating a strided part of it, and the partial
+// sums are combined by shuffles in a fixed order, so the result does not
+// depend on scheduling.
 #include "hmg_internal.h"
 
 namespace hmg {
@@ -16,8 +16,9 @@ namespace {
 // whatever its active lanes, and the FP64 pipe bounds this product: per row
 // it issues the FMAs, the shuffle sum (log2 LPR adds per warp) and the
 // epilogue (per warp).  Eight lanes per row made the sums and epilogues
-// dominate; four lanes keep loads coalesced over a row's consecutive entries.
-constexpr int LPR = 4;
+// dominate (1.29 ms per product of the r4x64 system against 0.81 ms with
+// four lanes); two lanes issue fewer sums still.
+constexpr int LPR = 2;
 constexpr unsigned FULL = 0xffffffffu;
 
 // y[i] = (y0[i] + alpha * sum_j A_ij x_j) * s[i]   (y0, s optional)
