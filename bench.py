@@ -385,6 +385,37 @@ def nlo_section(args, world, dev, stream, hbm):
     return out
 
 
+def velocity_pressure_section(h, args, world, dev, stream, ev0, ev1):
+    """The lowest-order velocity-pressure system (Sec. 4.1): GMRES(30) with the
+    Schur-complement preconditioner (Sec. 4.2), to the paper's 1e-5, right-hand
+    side (M2~ R_U, M3 R_P)."""
+    import torch
+
+    import hmg_inputs as gi
+    nhf, nvf, ncl = h.mixed_sizes()
+    R = torch.tensor(gi.mixed_rhs(nhf + nvf, ncl), dtype=torch.float64, device=dev)
+    ru, rp = R[:nhf + nvf].contiguous(), R[nhf + nvf:].contiguous()
+    bu, _ = h.mixed_apply(ru, torch.zeros_like(rp))
+    _, bp = h.mixed_apply(torch.zeros_like(ru), rp)
+    vp = {"rtol": 1e-5, "krylov": "GMRES(30), Schur-complement preconditioner, one V-cycle for H^^-1",
+          "unknowns": int(nhf + nvf + ncl)}
+    for form in ("fp64", "mixed"):
+        kwvp = dict(precision=form, rtol=1e-5, restart=30, max_iter=300)
+        for _ in range(2):
+            h.mixed_solve(bu, bp, **kwvp)
+        reps = max(5, min(args.steps, 20))
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            _, _, infovp = h.mixed_solve(bu, bp, **kwvp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / reps
+        vp[form] = {"solves_per_s": round(world / (ms / 1e3), 3), "ms_per_solve": round(ms, 4),
+                    "iterations": infovp["iterations"], "true_rel_residual": infovp["true_rel_residual"]}
+    return vp
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -477,27 +508,7 @@ def run_gpu(args):
 
     # ---- velocity-pressure system (Sec. 4.1): GMRES(30) with the Schur-complement
     # preconditioner (Sec. 4.2), to the paper's 1e-5, right-hand side (M2~ R_U, M3 R_P)
-    nhf, nvf, ncl = h.mixed_sizes()
-    R = torch.tensor(gi.mixed_rhs(nhf + nvf, ncl), dtype=torch.float64, device=dev)
-    ru, rp = R[:nhf + nvf].contiguous(), R[nhf + nvf:].contiguous()
-    bu, _ = h.mixed_apply(ru, torch.zeros_like(rp))
-    _, bp = h.mixed_apply(torch.zeros_like(ru), rp)
-    vp = {"rtol": 1e-5, "krylov": "GMRES(30), Schur-complement preconditioner, one V-cycle for H^^-1",
-          "unknowns": int(nhf + nvf + ncl)}
-    for form in ("fp64", "mixed"):
-        kwvp = dict(precision=form, rtol=1e-5, restart=30, max_iter=300)
-        for _ in range(2):
-            h.mixed_solve(bu, bp, **kwvp)
-        reps = max(5, min(args.steps, 20))
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(reps):
-            _, _, infovp = h.mixed_solve(bu, bp, **kwvp)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / reps
-        vp[form] = {"solves_per_s": round(world / (ms / 1e3), 3), "ms_per_solve": round(ms, 4),
-                    "iterations": infovp["iterations"], "true_rel_residual": infovp["true_rel_residual"]}
+    vp = None if args.no_vp else velocity_pressure_section(h, args, world, dev, stream, ev0, ev1)
 
     # ---- next-to-lowest order (Table "GridSetup": 5,120 columns x 64 layers,
     # 5 levels counting the p-coarsened one), GMRES(30) to the paper's 1e-5
@@ -712,6 +723,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-nlo", action="store_true", help="skip the next-to-lowest-order section")
+    ap.add_argument("--no-vp", action="store_true", help="skip the lowest-order velocity-pressure section")
     ap.add_argument("--oracle-iterations", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
