@@ -12,9 +12,10 @@
 // the forward results kept in a scratch vector (same lane, same thread).  The
 // per-cell coefficients (three 6 x 6 blocks per kernel) are the dominant
 // memory traffic; in FP64 the 6 x 6 products run on the FP64 pipe, which
-// bounds the kernels.  The mixed form runs the same kernels in FP32 (FP32
-// copies of the coefficients, FP32 work vectors), where the FP32 pipe leaves
-// them bound by memory.
+// bounds the kernels.  The mixed form runs the level in FP32 (FP32 copies of
+// the coefficients, FP32 work vectors): the operator and residual with the
+// same kernels, the column sweep with a variant that stages its operands in
+// shared memory, since in FP32 memory latency, not arithmetic, bounds it.
 #include <atomic>
 #include <stdexcept>
 #include <string>
@@ -103,11 +104,12 @@ __device__ __forceinline__ T nbr_dot(const Nbr<T>& n, const T (&v)[3][3]) {
 // uo = u + omega H^_z^-1 (b - H^ u) = (1 - omega) u + omega H^_z^-1 (b - H^_h u)
 // (u = nullptr: from zero).  omega is folded into Di.  T: arithmetic,
 // coefficients and u; TB: b (converted to T, and copied to bcopy when given);
-// TO: uo.  The warp walks its layers as a serial recurrence, so the operands
-// of the next PF layers are kept in flight in registers (staged slots
-// refilled as they are consumed).  PF = 1: four layers in flight measured
-// slower in FP32 (96.8 against 90.3 us at r4x64) and the FP64 pipe bounds the
-// FP64 kernel.
+// TO: uo.  Launched in FP64 (the FP32 sweep is k_nlo_sweep_staged).  The warp
+// walks its layers as a serial recurrence, so the operands of the next PF
+// layers are kept in flight in registers (staged slots refilled as they are
+// consumed).  PF = 1: the FP64 pipe bounds the kernel, and in FP32 four
+// layers in flight measured slower (96.8 against 90.3 us at r4x64) before the
+// shared-memory staging replaced it there.
 template <typename T>
 struct SweepPF {
   static constexpr int value = 1;
