@@ -977,6 +977,15 @@ void ensure_nlo_mixed(hmg_ctx* c) {
   if (!M.m2inv) {
     M.m2inv = dalloc<double>(c, M.nu);
     for (double** v : {&M.b, &M.x, &M.t1, &M.t2}) *v = dalloc<double>(c, M.n);
+    M.Dval32 = dalloc<float>(c, H.D.val.size());
+    M.Dtval32 = dalloc<float>(c, H.Dt.val.size());
+    M.tu32 = dalloc<float>(c, M.nu);
+    M.zp32 = dalloc<float>(c, M.np);
+  }
+  {
+    const std::vector<float> d32(H.D.val.begin(), H.D.val.end()), dt32(H.Dt.val.begin(), H.Dt.val.end());
+    cuda_ok(cudaMemcpy(M.Dval32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload");
+    cuda_ok(cudaMemcpy(M.Dtval32, dt32.data(), dt32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload");
   }
   std::vector<double> inv(H.m2diag.size());
   for (size_t i = 0; i < inv.size(); ++i) inv[i] = 1.0 / H.m2diag[i];
@@ -999,14 +1008,28 @@ hmg_status solve_nlo_mixed(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info
   sys.apply = [c, &M](const double* x, double* y, cudaStream_t st) {
     LAUNCH(c, HMG_K_APPLY, 0, st, launch_csr_spmv(M.A, x, 1.0, nullptr, nullptr, y, st));
   };
+  // The mixed form also runs the two outer factors' products with FP32
+  // values and operands (on the FP32 pipe); their sums and the FP64 right-hand
+  // sides they update stay FP64.
   sys.precond = [c, &M, &X, cfg, nz](const double* r, double* z, cudaStream_t st) {
     const double ac2 = c->ph.a * c->ph.c2;
-    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mul(M.nu, r, M.m2inv, M.t2, st));                 // M2inv r_U
-    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv(M.D, M.t2, -ac2, r + M.nu, nullptr, M.t2 + M.nu, st));
+    if (cfg.mixed) {
+      LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mul32(M.nu, r, M.m2inv, M.tu32, st));       // M2inv r_U
+      LAUNCH(c, HMG_K_ORTHO, 0, st,
+             launch_csr_spmv32(M.D, M.Dval32, M.tu32, -ac2, r + M.nu, nullptr, M.t2 + M.nu, st));
+    } else {
+      LAUNCH(c, HMG_K_ORTHO, 0, st, launch_mul(M.nu, r, M.m2inv, M.t2, st));           // M2inv r_U
+      LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv(M.D, M.t2, -ac2, r + M.nu, nullptr, M.t2 + M.nu, st));
+    }
     LAUNCH(c, HMG_K_LAYOUT, 0, st, launch_nlo_layout(X, nz, true, M.t2 + M.nu, X.t1, st));
     nlo_cycle(c, cfg, X.t1, X.t2, st);
     LAUNCH(c, HMG_K_LAYOUT, 0, st, launch_nlo_layout(X, nz, false, X.t2, z + M.nu, st));
-    LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv(M.Dt, z + M.nu, c->ph.a, r, M.m2inv, z, st));
+    if (cfg.mixed) {
+      LAUNCH(c, HMG_K_LAYOUT, 0, st, launch_convert(M.np, z + M.nu, HMG_FP64, M.zp32, st));
+      LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv32(M.Dt, M.Dtval32, M.zp32, c->ph.a, r, M.m2inv, z, st));
+    } else {
+      LAUNCH(c, HMG_K_ORTHO, 0, st, launch_csr_spmv(M.Dt, z + M.nu, c->ph.a, r, M.m2inv, z, st));
+    }
   };
   sys.orth = p.orth == 2 ? 2 : 1;
   sys.key = (4LL << 60) + (sys.orth == 2 ? (1LL << 59) : 0) + graph_key(cfg, true, 0);

@@ -174,6 +174,10 @@ struct DevCsr {
 void launch_csr_spmv(const DevCsr& A, const double* x, double alpha, const double* y0, const double* s, double* y,
                      cudaStream_t st);
 void launch_mul(int64_t n, const double* a, const double* b, double* y, cudaStream_t st);   // y = a * b
+// the same product with FP32 values and x, accumulated in FP32 (FP64 y0, s, y)
+void launch_csr_spmv32(const DevCsr& A, const float* val32, const float* x, double alpha, const double* y0,
+                       const double* s, double* y, cudaStream_t st);
+void launch_mul32(int64_t n, const double* a, const double* b, float* y, cudaStream_t st);  // y = a * b in FP32
 // The NLO velocity-pressure system on the device (NLO mixed COLUMN layout).
 struct NloMixedSys {
   bool ready = false;
@@ -181,6 +185,8 @@ struct NloMixedSys {
   DevCsr A, D, Dt;
   double* m2inv = nullptr;                                      // nu
   double *b = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr;   // n
+  // mixed form: FP32 values of D and D^T and FP32 operands of their products
+  float *Dval32 = nullptr, *Dtval32 = nullptr, *tu32 = nullptr, *zp32 = nullptr;
 };
 
 constexpr int NLO_TILE = 5;   // columns per warp: lanes 6 c5 + u, lanes 30 and 31 padding

@@ -21,35 +21,39 @@ namespace {
 constexpr int LPR = 2;
 constexpr unsigned FULL = 0xffffffffu;
 
-// y[i] = (y0[i] + alpha * sum_j A_ij x_j) * s[i]   (y0, s optional)
+// y[i] = (y0[i] + alpha * sum_j A_ij x_j) * s[i]   (y0, s optional).  TV, TX:
+// types of the matrix values and of x; TA: the accumulation (the mixed form's
+// preconditioner factors run in FP32 on the FP32 pipe); y, y0, s are FP64.
+template <typename TV, typename TX, typename TA>
 __global__ void k_csr_spmv(int64_t nrows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                           const double* __restrict__ val, const double* __restrict__ x, double alpha,
+                           const TV* __restrict__ val, const TX* __restrict__ x, double alpha,
                            const double* __restrict__ y0, const double* __restrict__ s, double* __restrict__ y) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = gid / LPR;
   const int sub = (int)(gid % LPR);
-  double acc = 0.0;
+  TA acc = TA(0);
   if (row < nrows) {
     // (four entries per lane loaded ahead of their use measured slower: 1.48
-    // against 1.29 ms for the r4x64 system)
+    // against 1.29 ms for the r4x64 system with eight lanes per row)
     const int64_t p1 = ptr[row + 1];
-    for (int64_t p = ptr[row] + sub; p < p1; p += LPR) acc = fma(val[p], x[col[p]], acc);
+    for (int64_t p = ptr[row] + sub; p < p1; p += LPR) acc = fma(TA(val[p]), TA(x[col[p]]), acc);
   }
 #pragma unroll
   for (int off = LPR / 2; off > 0; off >>= 1) acc += __shfl_down_sync(FULL, acc, off, LPR);
   if (row < nrows && sub == 0) {
-    double v = acc;
-    if (y0) v = fma(alpha, acc, y0[row]);
-    else if (alpha != 1.0) v = alpha * acc;
+    double v = double(acc);
+    if (y0) v = fma(alpha, v, y0[row]);
+    else if (alpha != 1.0) v = alpha * v;
     if (s) v *= s[row];
     y[row] = v;
   }
 }
 
+template <typename TY>
 __global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                      double* __restrict__ y) {
+                      TY* __restrict__ y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = a[i] * b[i];
+  if (i < n) y[i] = TY(a[i] * b[i]);
 }
 
 int grid_of(int64_t threads) { return (int)((threads + 255) / 256); }
@@ -58,11 +62,22 @@ int grid_of(int64_t threads) { return (int)((threads + 255) / 256); }
 
 void launch_csr_spmv(const DevCsr& A, const double* x, double alpha, const double* y0, const double* s, double* y,
                      cudaStream_t st) {
-  k_csr_spmv<<<grid_of(A.nrows * LPR), 256, 0, st>>>(A.nrows, A.ptr, A.col, A.val, x, alpha, y0, s, y);
+  k_csr_spmv<double, double, double><<<grid_of(A.nrows * LPR), 256, 0, st>>>(A.nrows, A.ptr, A.col, A.val, x, alpha,
+                                                                           y0, s, y);
+}
+
+void launch_csr_spmv32(const DevCsr& A, const float* val32, const float* x, double alpha, const double* y0,
+                       const double* s, double* y, cudaStream_t st) {
+  k_csr_spmv<float, float, float><<<grid_of(A.nrows * LPR), 256, 0, st>>>(A.nrows, A.ptr, A.col, val32, x, alpha,
+                                                                        y0, s, y);
 }
 
 void launch_mul(int64_t n, const double* a, const double* b, double* y, cudaStream_t st) {
-  k_mul<<<grid_of(n), 256, 0, st>>>(n, a, b, y);
+  k_mul<double><<<grid_of(n), 256, 0, st>>>(n, a, b, y);
+}
+
+void launch_mul32(int64_t n, const double* a, const double* b, float* y, cudaStream_t st) {
+  k_mul<float><<<grid_of(n), 256, 0, st>>>(n, a, b, y);
 }
 
 }  // namespace hmg
