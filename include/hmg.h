@@ -124,6 +124,25 @@ typedef struct hmg_ctx hmg_ctx;
  * caller and released with hmg_destroy.  Errors: INVALID_ARG, OOM, CUDA. */
 hmg_status hmg_build_hierarchy(const hmg_mesh_params* params, hmg_ctx** out);
 
+/* Device memory through the caller's allocator.  alloc(bytes, user) returns
+ * device memory of the current device (at least `bytes`, 256-byte aligned),
+ * or NULL when it cannot; release(ptr, user) takes back what alloc returned.
+ * The callbacks are called from the thread that calls into the library,
+ * only while no kernel of the context reads or writes that memory. */
+typedef void* (*hmg_alloc_fn)(size_t bytes, void* user);
+typedef void (*hmg_release_fn)(void* ptr, void* user);
+
+/* hmg_build_hierarchy with every device allocation of the context (levels,
+ * Krylov and GMRES vectors, the velocity-pressure and next-to-lowest-order
+ * tables, built later on first use) taken from alloc and returned with
+ * release by hmg_destroy, so a framework's memory pool (for instance a
+ * caching allocator) backs the context.  alloc returning NULL makes the call
+ * that needed the memory fail with HMG_ERR_OOM; the build releases what it
+ * had taken.  Page-locked host copies of the solver's scalars still come
+ * from the CUDA runtime.  Errors: INVALID_ARG (NULL callbacks), OOM, CUDA. */
+hmg_status hmg_build_hierarchy_with_allocator(const hmg_mesh_params* params, hmg_alloc_fn alloc,
+                                              hmg_release_fn release, void* user, hmg_ctx** out);
+
 /* Release every resource of a context (NULL is accepted). */
 hmg_status hmg_destroy(hmg_ctx* ctx);
 

@@ -78,8 +78,12 @@ class LevelInfo(ctypes.Structure):
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
+# hmg_alloc_fn / hmg_release_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _SIGNATURES = {
     "hmg_build_hierarchy": [ctypes.POINTER(MeshParams), ctypes.POINTER(_P)],
+    "hmg_build_hierarchy_with_allocator": [ctypes.POINTER(MeshParams), ALLOC_FN, RELEASE_FN, _P, ctypes.POINTER(_P)],
     "hmg_destroy": [_P],
     "hmg_get_level_info": [_P, _I, ctypes.POINTER(LevelInfo)],
     "hmg_export_mesh": [_P, _I, _P, _P],
@@ -158,14 +162,45 @@ class Workload:
     nlevels: int
 
 
-class Hierarchy:
-    """Mesh hierarchy plus assembled operator on the current CUDA device."""
+class Allocator:
+    """Device memory for a context from a caller's pair of callables:
+    alloc(nbytes) -> device pointer as int (0 or None when out of memory),
+    release(ptr).  The ctypes callbacks are kept alive with the object."""
 
-    def __init__(self, refinement, nlayers, nlevels, radius_m=6.371e6, thickness_m=1.0e4):
+    def __init__(self, alloc, release):
+        def _alloc(nbytes, user):
+            try:
+                return alloc(int(nbytes)) or None
+            except RuntimeError:          # the pool is exhausted
+                return None
+
+        def _release(ptr, user):
+            release(ptr)
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.release_fn = RELEASE_FN(_release)
+
+
+def torch_allocator(device=None):
+    """An Allocator backed by PyTorch's CUDA caching allocator."""
+    dev = torch.cuda.current_device() if device is None else device
+    return Allocator(lambda n: torch.cuda.caching_allocator_alloc(n, dev), torch.cuda.caching_allocator_delete)
+
+
+class Hierarchy:
+    """Mesh hierarchy plus assembled operator on the current CUDA device.
+    allocator: None (the CUDA runtime's cudaMalloc) or an Allocator, through
+    which every device allocation of the context goes."""
+
+    def __init__(self, refinement, nlayers, nlevels, radius_m=6.371e6, thickness_m=1.0e4, allocator=None):
         self.lib = load_library()
         self._ctx = _P()
+        self._allocator = allocator
         p = MeshParams(refinement, nlayers, nlevels, radius_m, thickness_m)
-        st = self.lib.hmg_build_hierarchy(ctypes.byref(p), ctypes.byref(self._ctx))
+        if allocator is None:
+            st = self.lib.hmg_build_hierarchy(ctypes.byref(p), ctypes.byref(self._ctx))
+        else:
+            st = self.lib.hmg_build_hierarchy_with_allocator(ctypes.byref(p), allocator.alloc_fn,
+                                                             allocator.release_fn, None, ctypes.byref(self._ctx))
         if st != HMG_OK:
             raise HMGError(st, self.lib.hmg_last_error(None).decode())
         self.refinement, self.nlayers, self.nlevels = refinement, nlayers, nlevels

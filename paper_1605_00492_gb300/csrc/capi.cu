@@ -36,11 +36,28 @@ void cuda_ok(cudaError_t e, const char* what) {
 
 void launched(const char* what) { cuda_ok(cudaGetLastError(), what); }
 
+// Device memory of a context: the caller's allocator when one was given,
+// else cudaMalloc; zero-filled.
+void* raw_alloc(hmg_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(bytes, c->alloc_user);
+    if (!p) throw Fail{HMG_ERR_OOM, "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes"};
+  } else {
+    cuda_ok(cudaMalloc(&p, bytes), "cudaMalloc");
+  }
+  return p;
+}
+
+void raw_free(hmg_ctx* c, void* p) {
+  if (c->release_fn) c->release_fn(p, c->alloc_user);
+  else cudaFree(p);
+}
+
 template <typename T>
 T* dalloc(hmg_ctx* c, size_t count) {
-  void* p = nullptr;
   if (count == 0) count = 1;
-  cuda_ok(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+  void* p = raw_alloc(c, count * sizeof(T));
   c->allocations.push_back(p);
   cuda_ok(cudaMemset(p, 0, count * sizeof(T)), "cudaMemset");
   return static_cast<T*>(p);
@@ -50,7 +67,7 @@ void dfree(hmg_ctx* c, void* p) {
   if (!p) return;
   auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
   if (it != c->allocations.end()) c->allocations.erase(it);
-  cudaFree(p);
+  raw_free(c, p);
 }
 
 void destroy_graph_prof(std::vector<GraphProf>& v) {
@@ -62,7 +79,7 @@ void destroy_graph_prof(std::vector<GraphProf>& v) {
 }
 
 void release(hmg_ctx* c) {
-  for (void* p : c->allocations) cudaFree(p);
+  for (void* p : c->allocations) raw_free(c, p);
   c->allocations.clear();
   if (c->host_sc) cudaFreeHost(c->host_sc);
   c->host_sc = nullptr;
@@ -1076,7 +1093,8 @@ const char* hmg_last_error(const hmg_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_build_error.c_str();
 }
 
-hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
+static hmg_status build_hierarchy(const hmg_mesh_params* p, hmg_alloc_fn alloc, hmg_release_fn rel, void* user,
+                                  hmg_ctx** out) {
   if (!out) {
     g_build_error = "out is NULL";
     return HMG_ERR_INVALID_ARG;
@@ -1085,6 +1103,7 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
   hmg_ctx* c = nullptr;
   hmg_status st = guarded(nullptr, [&] {
     require(p != nullptr, "params is NULL");
+    require((alloc == nullptr) == (rel == nullptr), "alloc and release must both be given");
     require(p->refinement >= 0 && p->refinement <= 10, "refinement must be in [0, 10]");
     require(p->nlayers >= 1 && p->nlayers <= 256, "nlayers must be in [1, 256]");
     require(p->nlevels >= 1 && p->nlevels <= p->refinement + 1, "nlevels must be in [1, refinement + 1]");
@@ -1092,6 +1111,9 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
     require(p->thickness_m > 0 && std::isfinite(p->thickness_m), "thickness_m must be positive");
     std::vector<HostLevel> host = build_mesh_hierarchy(p->refinement, p->nlevels);
     c = new hmg_ctx();
+    c->alloc_fn = alloc;
+    c->release_fn = rel;
+    c->alloc_user = user;
     c->mp = *p;
     c->lv.resize(host.size());
     for (size_t k = 0; k < host.size(); ++k) {
@@ -1172,6 +1194,19 @@ hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
   }
   *out = c;
   return HMG_OK;
+}
+
+hmg_status hmg_build_hierarchy(const hmg_mesh_params* p, hmg_ctx** out) {
+  return build_hierarchy(p, nullptr, nullptr, nullptr, out);
+}
+
+hmg_status hmg_build_hierarchy_with_allocator(const hmg_mesh_params* p, hmg_alloc_fn alloc, hmg_release_fn release,
+                                              void* user, hmg_ctx** out) {
+  if (!alloc || !release) {
+    g_build_error = "alloc and release must be non-NULL";
+    return HMG_ERR_INVALID_ARG;
+  }
+  return build_hierarchy(p, alloc, release, user, out);
 }
 
 hmg_status hmg_destroy(hmg_ctx* ctx) {

@@ -317,6 +317,10 @@ struct GraphProf {
 }  // namespace hmg
 
 struct hmg_ctx {
+  // caller's device allocator (both null: the CUDA runtime's)
+  hmg_alloc_fn alloc_fn = nullptr;
+  hmg_release_fn release_fn = nullptr;
+  void* alloc_user = nullptr;
   hmg_mesh_params mp{};
   hmg_op_params op{};
   hmg::Phys ph{};

@@ -51,3 +51,33 @@ def test_status_strings_and_argument_errors_without_gpu(lib):
     assert L.hmg_apply(None, 0, 0, 0, None, None, None) == 1
     assert L.hmg_solve(None, None, None, None, None, None) == 1
     assert L.hmg_destroy(None) == 0
+
+
+def test_allocator_hook_out_of_memory_without_gpu(lib):
+    """A caller allocator that refuses (returns NULL) makes the build fail
+    with HMG_ERR_OOM before any device work: the failure is made on the host
+    and the build releases what it had taken (nothing here).  NULL callbacks
+    are an argument error."""
+    import paper_1605_00492_gb300 as hmg
+    L = hmg.load_library()
+    calls = []
+
+    def refuse(nbytes):
+        calls.append(nbytes)
+        return None
+    released = []
+    alloc = hmg.Allocator(refuse, released.append)
+    ctx = ctypes.c_void_p()
+    p = hmg.MeshParams(2, 8, 2, 6.371e6, 1e4)
+    st = L.hmg_build_hierarchy_with_allocator(ctypes.byref(p), alloc.alloc_fn, alloc.release_fn, None,
+                                              ctypes.byref(ctx))
+    assert st == 3                         # HMG_ERR_OOM
+    assert b"allocator returned NULL" in L.hmg_last_error(None)
+    assert len(calls) == 1 and calls[0] > 0 and released == [] and not ctx.value
+    with pytest.raises(hmg.HMGError) as e:
+        hmg.Hierarchy(2, 8, 2, allocator=alloc)
+    assert e.value.status == 3
+    null_alloc = hmg.ALLOC_FN()
+    null_release = hmg.RELEASE_FN()
+    assert L.hmg_build_hierarchy_with_allocator(ctypes.byref(p), null_alloc, null_release, None,
+                                                ctypes.byref(ctx)) == 1
