@@ -417,6 +417,15 @@ hmg_status hmg_profile_start(hmg_ctx* ctx, unsigned kernel_mask, unsigned level_
  * records available.  Errors: INVALID_ARG, STATE (not started), CUDA. */
 hmg_status hmg_profile_stop(hmg_ctx* ctx, hmg_kernel_stat* out, int capacity, int* count);
 
+/* Convergence history of the last solve on this context (Sec. 6,
+ * convergence histories): after each Krylov iteration, the relative residual
+ * the stopping test used: ||r_k|| / ||b|| of the recursive residual for CG
+ * and flexible CG, the least-squares residual estimate for GMRES.  Up to
+ * `capacity` values are copied to the host buffer `out`; *count receives how
+ * many there are (the iteration count of the last solve).
+ * Errors: INVALID_ARG. */
+hmg_status hmg_residual_history(const hmg_ctx* ctx, double* out, int capacity, int* count);
+
 /* Number of kernels this context has launched since it was built. */
 hmg_status hmg_launch_count(const hmg_ctx* ctx, int64_t* count);
 

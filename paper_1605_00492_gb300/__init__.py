@@ -118,6 +118,7 @@ _SIGNATURES = {
     "hmg_profile_start": [_P, ctypes.c_uint, ctypes.c_uint],
     "hmg_profile_stop": [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)],
     "hmg_launch_count": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "hmg_residual_history": [_P, _P, _I, ctypes.POINTER(_I)],
     "hmg_kernel_name": [_I],
     "hmg_last_error": [_P],
     "hmg_status_string": [_I],
@@ -450,6 +451,16 @@ class Hierarchy:
         self._check(self.lib.hmg_profile_stop(self._ctx, buf, cap, ctypes.byref(n)))
         return {(KERNELS[buf[i].kernel], buf[i].level): (buf[i].launches, buf[i].total_ms)
                 for i in range(min(n.value, cap))}
+
+    def residual_history(self):
+        """Relative residual after each iteration of the last solve (numpy array)."""
+        import numpy as np
+        n = _I()
+        self._check(self.lib.hmg_residual_history(self._ctx, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        if n.value:
+            self._check(self.lib.hmg_residual_history(self._ctx, out.ctypes.data_as(_P), n.value, ctypes.byref(n)))
+        return out
 
     def launch_count(self):
         n = ctypes.c_int64()

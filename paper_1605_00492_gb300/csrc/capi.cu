@@ -417,6 +417,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   const bool flexible = cfg.mixed || p.krylov == HMG_KRYLOV_FCG;
   const size_t bytes = (size_t)L.Np * sizeof(double);
   hmg_solve_info inf{};
+  c->history.clear();
 
   cuda_ok(cudaEventRecord(c->ev0, s), "event");
   cuda_ok(cudaMemsetAsync(c->red.sc, 0, S_COUNT * sizeof(double), s), "memset");
@@ -455,6 +456,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
       const int flag = (int)c->host_sc[S_FLAG];
       const double rr = c->host_sc[S_RR];
       inf.rel_residual = std::sqrt(rr / bb);
+      c->history.push_back(inf.rel_residual);
       if (flag & F_NONFINITE) {
         st = HMG_ERR_NONFINITE;
         break;
@@ -566,6 +568,7 @@ hmg_status gmres_run(hmg_ctx* c, const KrylovSystem& sys, const hmg_solve_params
   const int64_t ld = sys.n;
   ensure_gmres(c, m, ld);
   hmg_solve_info inf{};
+  c->history.clear();
 
   cuda_ok(cudaEventRecord(c->ev0, s), "event");
   cuda_ok(cudaMemsetAsync(c->red.sc, 0, S_COUNT * sizeof(double), s), "memset");
@@ -633,6 +636,7 @@ hmg_status gmres_run(hmg_ctx* c, const KrylovSystem& sys, const hmg_solve_params
         jend = j + 1;
         inf.iterations = k;
         inf.rel_residual = std::fabs(g[j + 1]) / r0;
+        c->history.push_back(inf.rel_residual);
         if (inf.rel_residual < p.rtol) {
           inf.converged = 1;
           st = HMG_OK;
@@ -1662,6 +1666,14 @@ hmg_status hmg_profile_stop(hmg_ctx* ctx, hmg_kernel_stat* out, int capacity, in
     if (count) *count = (int)agg.size();
     for (int i = 0; out && i < capacity && i < (int)agg.size(); ++i) out[i] = agg[i];
   });
+}
+
+hmg_status hmg_residual_history(const hmg_ctx* ctx, double* out, int capacity, int* count) {
+  if (!ctx || !count || capacity < 0 || (capacity > 0 && !out)) return HMG_ERR_INVALID_ARG;
+  *count = (int)ctx->history.size();
+  const size_t k = std::min(ctx->history.size(), (size_t)capacity);
+  if (k) std::memcpy(out, ctx->history.data(), k * sizeof(double));
+  return HMG_OK;
 }
 
 hmg_status hmg_launch_count(const hmg_ctx* ctx, int64_t* count) {

@@ -345,6 +345,8 @@ struct hmg_ctx {
   bool capturing = false;
   std::vector<hmg::GraphProf> capture_prof;       // events of the graph being captured
   int64_t launches = 0;
+  // relative recursive residual after each iteration of the last solve
+  std::vector<double> history;
   // CUDA graphs of the Krylov iteration body, one per cycle configuration
   struct BodyGraph {
     int64_t key = -1;

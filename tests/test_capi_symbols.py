@@ -81,3 +81,10 @@ def test_allocator_hook_out_of_memory_without_gpu(lib):
     null_release = hmg.RELEASE_FN()
     assert L.hmg_build_hierarchy_with_allocator(ctypes.byref(p), null_alloc, null_release, None,
                                                 ctypes.byref(ctx)) == 1
+
+
+def test_residual_history_argument_errors_without_gpu(lib):
+    import paper_1605_00492_gb300 as hmg
+    L = hmg.load_library()
+    n = ctypes.c_int()
+    assert L.hmg_residual_history(None, None, 0, ctypes.byref(n)) == 1
