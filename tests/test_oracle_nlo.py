@@ -424,3 +424,26 @@ def test_nlo_matrices_by_prism_quadrature():
                                 sum(wz * eta(z)[mm] * dzeta(z) for z, wz in zip(zq, zw))
                             assert Dz[nlo.pdof(c, layer, jv, mm, nz), f] == pytest.approx(q, abs=1e-7 * max(1, abs(q)))
                 assert nop.mz[f] == pytest.approx(mass_q, rel=1e-9)
+
+
+@pytest.mark.parametrize("nz", [1, 2])
+def test_nlo_short_columns(nz):
+    """One and two layers: the vertical velocity has only the middle nodes
+    (and one interface); H^ stays SPD with H^ 1 = M3 1, the column solve is
+    exact for decoupled columns and the V-cycle is symmetric."""
+    ms = mesh.hierarchy(1, 2)
+    prm = helmholtz.Params(refinement=1, nlayers=nz)
+    nop = nlo.assemble_nlo(ms[0], prm)
+    lo = helmholtz.assemble_hierarchy(ms, prm)
+    assert nop.mz.size == ms[0].ncols * 3 * (2 * nz - 1)
+    H = nop.H.toarray()
+    assert np.abs(H - H.T).max() <= 1e-14 * np.abs(H).max()
+    assert np.linalg.eigvalsh(H).min() > 0
+    one = np.ones(nop.n)
+    assert np.allclose(nop.H @ one, nop.M3 @ one, rtol=1e-9)
+    b = RNG.standard_normal(nop.n)
+    import dataclasses
+    u = nlo.smooth(dataclasses.replace(nop, H=nop.Hz), np.zeros(nop.n), b, 1.0)
+    assert np.linalg.norm(nop.Hz @ u - b) <= 1e-12 * np.linalg.norm(b)
+    x, y = RNG.standard_normal(nop.n), RNG.standard_normal(nop.n)
+    assert abs(y @ nlo.vcycle(nop, lo, x) - x @ nlo.vcycle(nop, lo, y)) <= 1e-12 * abs(y @ nlo.vcycle(nop, lo, x))
