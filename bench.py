@@ -102,6 +102,24 @@ def kernel_bytes_per_cell(kernel, s, nz, s_b=None, s_out=None, s_c=None, fused_p
 KERNEL_FLOPS = {"sweep0": 5, "sweep": 13, "resid_restrict": 12.5, "prolong": 1, "apply": 11}
 
 
+def useful_bandwidth(breakdown, levels_ncells, nz, hbm_gbs):
+    """Per kernel class and level of an FP64 solve, the paper's "useful
+    bandwidth" (Sec. 5.4, performance model): model bytes of all launches over
+    their traced time, with the FP64 rate beside it (the GB300 bound of these
+    kernels).  breakdown: {(kernel, level): (launches, ms)}."""
+    out = {}
+    for (k, lev), (n, ms) in sorted(breakdown.items(), key=lambda kv: (kv[0][1], kv[0][0])):
+        if k not in KERNEL_FLOPS or ms <= 0:
+            continue
+        cells = levels_ncells[lev]
+        gbs = kernel_bytes_per_cell(k, 8, nz) * cells * n / (ms * 1e-3) / 1e9
+        tfl = KERNEL_FLOPS[k] * cells * n / (ms * 1e-3) / 1e12
+        out[f"{k}@{lev}"] = {"launches": n, "us_per_launch": round(1e3 * ms / n, 2), "GB_s": round(gbs, 1),
+                             "frac_hbm": round(gbs / hbm_gbs, 4), "TFLOP_s": round(tfl, 4),
+                             "frac_fp64": round(tfl / FP64_PEAK_TFLOPS, 4)}
+    return out
+
+
 def vcycle_bytes(levels_ncells, nz, mixed, nu_pre=2, nu_post=2, n_coarse=2):
     """Model bytes of one V-cycle (sum of its kernels)."""
     total = 0.0
@@ -575,6 +593,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "breakdown_fp64_one_solve": breakdown(br64),
+        "useful_bandwidth_fp64": useful_bandwidth(br64, ncells_levels, nz, hbm),
         "breakdown_mixed_one_solve": breakdown(brmx),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

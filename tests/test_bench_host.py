@@ -75,3 +75,16 @@ def test_max_over_ranks_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
     assert res == {0: 11.0, 1: 11.0}
+
+
+def test_useful_bandwidth_from_a_breakdown():
+    """Model bytes and FP64 flops of each kernel class over its traced time."""
+    br = {("sweep", 0): (3, 0.3), ("apply", 0): (1, 0.08), ("dot", 0): (1, 0.02), ("sweep0", 1): (2, 0.04)}
+    cells = [5_242_880, 1_310_720]
+    ub = bench.useful_bandwidth(br, cells, 64, 6795.5)
+    assert set(ub) == {"sweep@0", "apply@0", "sweep0@1"}          # kernels without a byte model are left out
+    per_cell = bench.kernel_bytes_per_cell("sweep", 8, 64)
+    assert ub["sweep@0"]["GB_s"] == pytest.approx(per_cell * cells[0] * 3 / 0.3e-3 / 1e9, rel=1e-3)
+    assert ub["sweep@0"]["us_per_launch"] == pytest.approx(100.0)
+    assert ub["apply@0"]["TFLOP_s"] == pytest.approx(11 * cells[0] / 0.08e-3 / 1e12, rel=1e-3)
+    assert 0 < ub["sweep0@1"]["frac_hbm"] < 1
