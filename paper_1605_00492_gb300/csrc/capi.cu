@@ -1077,6 +1077,12 @@ void need_assembled(const hmg_ctx* c) {
 
 }  // namespace
 
+namespace hmg {
+// Tracing hooks for entry points defined in other files (see LAUNCH above).
+int trace_begin(hmg_ctx* c, int kernel, int level, cudaStream_t s) { return prof_begin(c, kernel, level, s); }
+void trace_end(hmg_ctx* c, int rec, cudaStream_t s) { prof_end(c, rec, s); }
+}  // namespace hmg
+
 extern "C" {
 
 const char* hmg_status_string(hmg_status s) {

@@ -775,13 +775,6 @@ inline ParCfg par_cfg(const Level& L, bool fp32 = false) {
   return {nt * rg, rg};
 }
 
-template <typename K>
-void allow_smem(K kern, size_t smem, size_t& configured) {
-  if (smem > 48 * 1024 && configured < smem) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
-}
 
 template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT, bool TW2>
 void tsweep_k(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
@@ -789,8 +782,8 @@ void tsweep_k(const Level& L, const void* b, const void* u, void* uo, const void
   auto kern = k_tsweep<T, TB, TO, MODE, TE, NW, DOT, TW2>;
   size_t smem = (2 * (size_t)L.nz + 2) * TW * sizeof(T);
   if (DOT && smem < (size_t)DOT * NW * 32 * sizeof(double)) smem = (size_t)DOT * NW * 32 * sizeof(double);
-  static size_t configured = 0;
-  allow_smem(kern, smem, configured);
+  static SmemOptIn opt_in;
+  allow_smem(kern, smem, opt_in);
   Reduce red = dot ? dot->red : Reduce{};
   kern<<<ntiles_of(L), NW * 32, smem, s>>>(view<T>(L), (const TB*)b, (const T*)u, (TO*)uo, (const TE*)ec, bcopy,
                                           (T)(1.0 - omega), dot ? dot->a : nullptr, dot ? dot->c : nullptr, red);
@@ -821,8 +814,8 @@ void asweep_k(const Level& L, const void* b, const void* u, void* uo, float* bco
   // b, then lo, w, u (R for MODE_ZERO) and, for MODE_PLAIN, three neighbour arrays, then 2 twist rows
   size_t smem = cells * sizeof(TB) + (MODE == MODE_ZERO ? 3 : 6) * cells * 4 + 2 * TW * 4;
   if (DOT && smem < (size_t)DOT * NW * 32 * sizeof(double)) smem = (size_t)DOT * NW * 32 * sizeof(double);
-  static size_t configured = 0;
-  allow_smem(kern, smem, configured);
+  static SmemOptIn opt_in;
+  allow_smem(kern, smem, opt_in);
   Reduce red = dot ? dot->red : Reduce{};
   kern<<<ntiles_of(L), NW * 32, smem, s>>>(view<float>(L), (const TB*)b, (const float*)u, (TO*)uo, bcopy,
                                           (float)(1.0 - omega), dot ? dot->a : nullptr, dot ? dot->c : nullptr,

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -314,6 +315,37 @@ struct GraphProf {
   int kernel, level;
   cudaEvent_t a, b;
 };
+}  // namespace hmg
+
+struct hmg_ctx;
+namespace hmg {
+// Dynamic shared memory above 48 KB needs a per-kernel opt-in, and the
+// attribute belongs to the device that is current when it is set.  One
+// SmemOptIn per kernel instantiation records, per device ordinal, the largest
+// size set so far; the mutex keeps host threads from racing on it.
+struct SmemOptIn {
+  std::mutex m;
+  size_t bytes[64] = {};
+};
+template <typename K>
+cudaError_t allow_smem(K kern, size_t smem, SmemOptIn& st) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(st.m);
+  size_t& cur = st.bytes[dev & 63];
+  if (cur >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) cur = smem;
+  return e;
+}
+
+// Bracket a launch with the tracing events of hmg_profile_start when tracing
+// selects (kernel, level); trace_begin returns the record to hand to
+// trace_end (-1: not traced).  Both may throw on a CUDA error.
+int trace_begin(hmg_ctx* c, int kernel, int level, cudaStream_t s);
+void trace_end(hmg_ctx* c, int rec, cudaStream_t s);
 }  // namespace hmg
 
 struct hmg_ctx {

@@ -186,11 +186,8 @@ void transpose(bool to_tiled, int nitems, int nz, int nzc, const void* src, void
   const int ntiles = (nitems + TW - 1) / TW;
   const int g = ntiles < 152 * 8 ? ntiles : 152 * 8;
   const size_t smem = (size_t)nz * 33 * sizeof(T);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
-    cudaFuncSetAttribute(k_transpose<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  static SmemOptIn opt_in;
+  allow_smem(k_transpose<T>, smem, opt_in);
   k_transpose<T><<<g, 256, smem, s>>>(to_tiled, nitems, nz, nzc, ntiles, (const T*)src, (T*)dst);
 }
 

@@ -2,7 +2,10 @@
 // hmg_apply, with its two tiled staging vectors held in a fixed device array
 // of this file instead of memory allocated for the context.  It calls no
 // allocating function (no cudaMalloc / cudaFree, no library allocator).
+#include <exception>
 #include <mutex>
+#include <new>
+#include <string>
 
 #include "hmg_internal.h"
 
@@ -48,8 +51,9 @@ cudaError_t scratch_on_current_device(double** out, std::string& why) {
 
 }  // namespace
 
-extern "C" hmg_status hmg_apply_noalloc(hmg_ctx* ctx, int level, const double* x, double* y, void* stream) {
-  if (!ctx) return HMG_ERR_INVALID_ARG;
+namespace {
+
+hmg_status apply_noalloc(hmg_ctx* ctx, int level, const double* x, double* y, void* stream) {
   if (level < 0 || level >= (int)ctx->lv.size()) {
     ctx->err = "bad level";
     return HMG_ERR_INVALID_ARG;
@@ -79,9 +83,16 @@ extern "C" hmg_status hmg_apply_noalloc(hmg_ctx* ctx, int level, const double* x
   double* xt = scratch;
   double* yt = scratch + HMG_NOALLOC_MAX_CELLS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // The three launches are traced like hmg_apply's (hmg_profile_start).
+  int rec = trace_begin(ctx, HMG_K_LAYOUT, level, s);
   launch_to_tiled(L, HMG_FP64, x, xt, s);
+  trace_end(ctx, rec, s);
+  rec = trace_begin(ctx, HMG_K_APPLY, level, s);
   launch_apply(L, HMG_FP64, xt, yt, nullptr, s);
+  trace_end(ctx, rec, s);
+  rec = trace_begin(ctx, HMG_K_LAYOUT, level, s);
   launch_to_column(L, HMG_FP64, yt, y, s);
+  trace_end(ctx, rec, s);
   ctx->launches += 3;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -90,4 +101,23 @@ extern "C" hmg_status hmg_apply_noalloc(hmg_ctx* ctx, int level, const double* x
   }
   ctx->err.clear();
   return HMG_OK;
+}
+
+}  // namespace
+
+// No exception leaves the C ABI: host allocation failures (the error strings)
+// map to HMG_ERR_OOM, a CUDA error raised while tracing to HMG_ERR_CUDA.
+extern "C" hmg_status hmg_apply_noalloc(hmg_ctx* ctx, int level, const double* x, double* y, void* stream) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  try {
+    return apply_noalloc(ctx, level, x, y, stream);
+  } catch (const std::bad_alloc&) {
+    return HMG_ERR_OOM;
+  } catch (const std::exception& e) {
+    ctx->err = e.what();
+    return HMG_ERR_CUDA;
+  } catch (...) {
+    ctx->err = "hmg_apply_noalloc: CUDA error while tracing";
+    return HMG_ERR_CUDA;
+  }
 }

@@ -138,3 +138,52 @@ def test_flexible_cg_agrees_with_cg_for_a_linear_preconditioner():
     x2, i2 = krylov.fpcg(ops[0].H.dot, P, b, rtol=1e-8)
     assert abs(i1.iterations - i2.iterations) <= 1
     assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-7
+
+
+def _conjugacy_of_successive_directions(solver, ops, b, max_iter):
+    """Run `solver` with a preconditioner that changes between calls (V-cycles
+    alternating between 1 and 3 smoothing steps, so not a fixed linear map)
+    and return max_k |p_k^T H p_(k-1)| / (||p_k||_H ||p_(k-1)||_H) over the
+    search directions p_k, which are exactly the vectors the solver hands to
+    the operator."""
+    H = ops[0].H
+    calls = [0]
+
+    def precond(v):
+        nu = 1 if calls[0] % 2 == 0 else 3
+        calls[0] += 1
+        return multigrid.vcycle(ops, v, nu_pre=nu, nu_post=nu)
+
+    dirs = []
+
+    def apply_A(p):
+        dirs.append(p.copy())
+        return H.dot(p)
+
+    solver(apply_A, precond, b, rtol=1e-14, max_iter=max_iter)
+    worst = 0.0
+    for p1, p0 in zip(dirs[1:], dirs[:-1]):
+        Hp0 = H.dot(p0)
+        den = np.sqrt(np.dot(p1, H.dot(p1)) * np.dot(p0, Hp0))
+        worst = max(worst, abs(np.dot(p1, Hp0)) / den)
+    return worst, len(dirs)
+
+
+def test_flexible_cg_keeps_successive_directions_conjugate_for_a_varying_preconditioner():
+    """Flexible CG (Polak-Ribiere beta = z_k.(r_k - r_(k-1)) / z_(k-1).r_(k-1)):
+    with alpha_(k-1) = z_(k-1).r_(k-1) / p_(k-1).H p_(k-1) and
+    r_k - r_(k-1) = -alpha_(k-1) H p_(k-1), beta equals
+    -z_k.H p_(k-1) / p_(k-1).H p_(k-1), so p_k = z_k + beta p_(k-1) is
+    H-conjugate to p_(k-1) whatever z_k the preconditioner returns.  The
+    Fletcher-Reeves beta of plain CG (z_k.r_k / z_(k-1).r_(k-1)) has that
+    property only when z_k.r_(k-1) = 0, i.e. for a fixed symmetric
+    preconditioner; with the alternating V-cycle it loses it, which the
+    second half of the test shows, so a flexible CG that silently used the
+    plain-CG beta fails here."""
+    _, _, ops = _ops(3, 16, 3)
+    b = gi.rhs(ops[0].ncells)
+    worst, n = _conjugacy_of_successive_directions(krylov.fpcg, ops, b, 8)
+    assert n == 8
+    assert worst < 1e-10
+    worst_plain, _ = _conjugacy_of_successive_directions(krylov.pcg, ops, b, 8)
+    assert worst_plain > 1e-4
