@@ -150,7 +150,7 @@ def vcycle_bytes(levels_ncells, nz, mixed, nu_pre=2, nu_post=2, n_coarse=2):
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 100 ms) during the timed region."""
 
     QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -436,6 +436,138 @@ def velocity_pressure_section(h, args, world, dev, stream, ev0, ev1):
     return vp
 
 
+def timed_steps(fn, steps, stream):
+    """Run fn() `steps` times between CUDA events recorded on `stream` (one
+    event before each step and one after the last, no synchronisation in
+    between).  Returns (total ms, [ms of each step])."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(steps):
+        fn()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    return evs[0].elapsed_time(evs[-1]), per
+
+
+def step_stats(per):
+    return {"min": round(min(per), 4), "median": round(statistics.median(per), 4), "max": round(max(per), 4)}
+
+
+def small_config_section(args, dev, stream):
+    """The r3x16 workload (20,480 cells, 3 levels): L2-resident and bound by
+    launch latency, reported as latency per FP64 solve."""
+    import torch
+
+    import hmg_inputs as gi
+    import paper_1605_00492_gb300 as hmg
+    w = gi.WORKLOADS["r3x16"]
+    h = hmg.Hierarchy(w["refinement"], w["nlayers"], w["nlevels"])
+    h.assemble()
+    b = torch.tensor(gi.rhs(h.ncells), dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    kw = dict(precision="fp64", krylov="cg", rtol=1e-8, max_iter=200)
+    for _ in range(5):
+        _, info = h.solve(b, out=x, **kw)
+    reps = max(20, args.steps)
+    total, per = timed_steps(lambda: h.solve(b, out=x, **kw), reps, stream)
+    h.close()
+    return {"workload": "r3x16: " + workload_desc("r3x16"), "ncells": int(b.numel()),
+            "latency_ms": step_stats(per), "solves_per_s": round(reps / (total / 1e3), 2),
+            "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+            "note": "L2-resident and launch-latency bound: not counted against HBM"}
+
+
+def adjoint_section(args, dev, stream):
+    """Forward + backward of the differentiable solve p = H^(theta)^-1 b at
+    r5x64 (1,310,720 cells, 5 levels): loss 1/2 |p - p_t|^2, gradients with
+    respect to b and theta (assembly from theta, forward CG solve, re-assembly,
+    adjoint CG solve, face contraction), FP64, CG to 1e-8 both ways."""
+    import torch
+
+    import hmg_inputs as gi
+    import paper_1605_00492_gb300 as hmg
+    from paper_1605_00492_gb300.autograd import HelmholtzSolve
+    w = gi.WORKLOADS["r5x64a"]
+    t0 = time.perf_counter()
+    h = hmg.Hierarchy(w["refinement"], w["nlayers"], w["nlevels"])
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    n = h.ncells
+    b0 = torch.tensor(gi.rhs(n), dtype=torch.float64, device=dev)
+    th0 = torch.tensor(gi.theta(n), dtype=torch.float64, device=dev)
+    pt = torch.tensor(gi.ptarget(n), dtype=torch.float64, device=dev)
+    kw = dict(precision="fp64", krylov="cg", rtol=1e-8, max_iter=200)
+
+    def step():
+        b = b0.clone().requires_grad_(True)
+        th = th0.clone().requires_grad_(True)
+        p = HelmholtzSolve.apply(h, b, th, kw)
+        loss = 0.5 * torch.sum((p - pt) ** 2)
+        loss.backward()
+        return b.grad, th.grad
+
+    for _ in range(3):
+        step()
+    reps = max(5, min(args.steps, 20))
+    total, per = timed_steps(step, reps, stream)
+    # forward alone, same protocol
+    def fwd():
+        with torch.no_grad():
+            HelmholtzSolve.apply(h, b0, th0, kw)
+    totf, _ = timed_steps(fwd, reps, stream)
+    h.close()
+    return {"workload": "r5x64a: " + workload_desc("r5x64a") + ", theta = exp(0.3 N(0,1)) per cell",
+            "ncells": n, "fwd_bwd_ms": step_stats(per), "fwd_bwd_per_s": round(reps / (total / 1e3), 3),
+            "fwd_ms": round(totf / reps, 4), "build_s": round(t_build, 3),
+            "what": "assemble(theta) + CG solve; backward: assemble(theta) + adjoint CG solve + theta face "
+                    "contraction; loss 1/2|p - p_t|^2"}
+
+
+def large_config_section(args, dev, stream, hbm):
+    """The r7x128 workload (327,680 columns x 128 layers = 41.9 M cells, 6
+    levels), both forms: solves/s and the V-cycle's model bytes over time."""
+    import torch
+
+    import hmg_inputs as gi
+    import paper_1605_00492_gb300 as hmg
+    w = gi.WORKLOADS["r7x128"]
+    t0 = time.perf_counter()
+    h = hmg.Hierarchy(w["refinement"], w["nlayers"], w["nlevels"])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    h.assemble()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    n = h.ncells
+    b = torch.tensor(gi.rhs(n), dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    out = {"workload": "r7x128: " + workload_desc("r7x128"), "ncells": n,
+           "setup_s": {"build_hierarchy": round(t1 - t0, 3), "assemble": round(t2 - t1, 3)}}
+    ncl = [lv["ncells"] for lv in h.levels]
+    rt = h.to_layout(b, "column", "tiled")
+    zt = torch.empty_like(rt)
+    reps = max(5, min(args.steps, 10))
+    for form, kw in (("fp64", dict(precision="fp64", krylov="cg")), ("mixed", dict(precision="mixed", krylov="fcg"))):
+        kw.update(rtol=1e-8, max_iter=200)
+        for _ in range(2):
+            _, info = h.solve(b, out=x, **kw)
+        total, per = timed_steps(lambda: h.solve(b, out=x, **kw), reps, stream)
+        for _ in range(2):
+            h.vcycle(rt, precision=form, layout="tiled", out=zt)
+        vt, _ = timed_steps(lambda: h.vcycle(rt, precision=form, layout="tiled", out=zt), reps, stream)
+        byts = vcycle_bytes(ncl, w["nlayers"], form == "mixed")
+        gbs = byts / (vt / reps * 1e-3) / 1e9
+        out[form] = {"solves_per_s": round(reps / (total / 1e3), 3), "ms_per_solve": step_stats(per),
+                     "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+                     "vcycle": {"ms": round(vt / reps, 4), "model_bytes": int(byts), "GB_s": round(gbs, 1),
+                                "frac_of_hbm_peak": round(gbs / hbm, 4)}}
+    h.close()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -451,8 +583,18 @@ def run_gpu(args):
     import paper_1605_00492_gb300 as hmg
     w = gi.WORKLOADS[args.workload]
     r, nz, L = w["refinement"], w["nlayers"], w["nlevels"]
+    # ---- setup, timed apart from the solves (the paper's t_setup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     h = hmg.Hierarchy(r, nz, L)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     h.assemble()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    setup = {"build_hierarchy_s": round(t1 - t0, 4), "assemble_s": round(t2 - t1, 4),
+             "what": "host mesh and hierarchy generation with its upload; device assembly of every level "
+                     "(first call, FP32 copies included)"}
     n = h.ncells
     stream = torch.cuda.current_stream()
     b = torch.tensor(gi.rhs(n), dtype=torch.float64, device=dev)
@@ -472,37 +614,40 @@ def run_gpu(args):
     _, infomx = h.solve(b, out=x, **kwmx)
     brmx = h.profile_stop()
     (dom_k, dom_l), _ = max(br64.items(), key=lambda kv: kv[1][1])
+    for _ in range(args.warmup):
+        h.solve(b, out=x, **kw64)
 
-    # ---- timed region: K FP64 solves, dominant kernel traced live
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- timed region: K FP64 solves, nothing traced (each solve is one
+    # device-side CG loop); clocks sampled by nvidia-smi meanwhile
     launches0 = h.launch_count()
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        h.profile_start(kernels=[dom_k], levels=[dom_l])
         clk.mark(True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            _, info = h.solve(b, out=x, **kw64)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        elapsed_ms, per64 = timed_steps(lambda: h.solve(b, out=x, **kw64), args.steps, stream)
         clk.mark(False)
-        dom_stats = h.profile_stop()
     barrier(world)
     launches = h.launch_count() - launches0
-    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    _, info = h.solve(b, out=x, **kw64)
+    x64 = x.clone()
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
     clocks = clk.summary()
     ms64 = elapsed_ms / args.steps
     value = world * args.steps / (elapsed_ms / 1e3)
 
+    # ---- the dominant kernel, traced live over K more solves (after the
+    # timed region, so that tracing does not perturb the headline)
+    h.profile_start(kernels=[dom_k], levels=[dom_l])
+    traced_ms, _ = timed_steps(lambda: h.solve(b, out=x, **kw64), args.steps, stream)
+    dom_stats = h.profile_stop()
+
     # ---- mixed form, same protocol (no tracing)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        _, infomx = h.solve(b, out=x, **kwmx)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    msmx = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    for _ in range(3):
+        h.solve(b, out=x, **kwmx)
+    totmx, permx = timed_steps(lambda: h.solve(b, out=x, **kwmx), args.steps, stream)
+    msmx = max_over_ranks(totmx, world, dev) / args.steps
+    _, infomx = h.solve(b, out=x, **kwmx)
+    err_mx = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
 
     # ---- V-cycle alone (tiled layout, no conversions), both forms
     hbm, hbm_src = measured_peaks()
@@ -514,13 +659,8 @@ def run_gpu(args):
         for _ in range(3):
             h.vcycle(rt, precision=form, layout="tiled", out=zt)
         reps = max(10, args.steps)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(reps):
-            h.vcycle(rt, precision=form, layout="tiled", out=zt)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / reps
+        vt, _ = timed_steps(lambda: h.vcycle(rt, precision=form, layout="tiled", out=zt), reps, stream)
+        ms = vt / reps
         byts = vcycle_bytes(ncells_levels, nz, form == "mixed")
         gbs = byts / (ms * 1e-3) / 1e9
         vc[form] = {"ms": round(ms, 4), "model_bytes": int(byts), "GB_s": round(gbs, 1),
@@ -528,6 +668,7 @@ def run_gpu(args):
 
     # ---- velocity-pressure system (Sec. 4.1): GMRES(30) with the Schur-complement
     # preconditioner (Sec. 4.2), to the paper's 1e-5, right-hand side (M2~ R_U, M3 R_P)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     vp = None if args.no_vp else velocity_pressure_section(h, args, world, dev, stream, ev0, ev1)
 
     # ---- next-to-lowest order (Table "GridSetup": 5,120 columns x 64 layers,
@@ -541,15 +682,16 @@ def run_gpu(args):
         xh = torch.empty_like(bh).pin_memory()
         for _ in range(2):
             h.solve_host(bh, xh, **kw64)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            h.solve_host(bh, xh, **kw64)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms_e2e = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+        tot_e2e, per_e2e = timed_steps(lambda: h.solve_host(bh, xh, **kw64), args.steps, stream)
+        ms_e2e = max_over_ranks(tot_e2e, world, dev) / args.steps
         e2e = {"value": round(world / (ms_e2e / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": int(n * 8),
-               "d2h_bytes_per_step": int(n * 8), "ms_per_step": round(ms_e2e, 4)}
+               "d2h_bytes_per_step": int(n * 8), "ms_per_step": round(ms_e2e, 4),
+               "ms_per_step_stats": step_stats(per_e2e)}
+
+    # ---- the other workloads: r3x16 latency, r5x64a adjoint, r7x128 both forms
+    small = None if args.no_extra else small_config_section(args, dev, stream)
+    adjoint = None if args.no_extra else adjoint_section(args, dev, stream)
+    large = None if (args.no_extra or args.no_large) else large_config_section(args, dev, stream, hbm)
 
     # ---- roofline of the dominant kernel
     cnt, tot = dom_stats.get((dom_k, dom_l), (0, 0.0))
@@ -569,6 +711,9 @@ def run_gpu(args):
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(gbs / hbm, 4), "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
     roof.update({"kernel": f"{dom_k}@level{dom_l}", "launches": cnt, "avg_us": round(avg_ms * 1e3, 2),
+                 "timing": (f"CUDA events around each launch of the kernel inside the captured iteration graphs of "
+                            f"{args.steps} FP64 solves traced right after the timed region "
+                            f"({round(traced_ms / args.steps, 4)} ms per traced solve)"),
                  "bytes_per_launch": int(per_cell_b * n_l), "flops_per_launch": int(KERNEL_FLOPS[dom_k] * n_l),
                  "traffic": args.traffic if args.traffic is not None else
                  (TRAFFIC_SWEEP_L0_R6X64 if (args.workload == "r6x64" and (dom_k, dom_l) == ("sweep", 0)) else None)})
@@ -583,10 +728,17 @@ def run_gpu(args):
         "config": {"workload": f"{args.workload}: {workload_desc(args.workload)}", "ncols": h.levels[0]["ncols"], "nlayers": nz,
                    "ncells": n, "nlevels": L, "rhs": "N(0,1) per cell, seed 0", "krylov": "CG",
                    "l2": "working set > 1 GB, larger than the 126 MB L2: no flush"},
+        "ms_per_step_stats": step_stats(per64),
         "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+        "setup": setup,
         "mixed": {"solves_per_s": round(world / (msmx / 1e3), 3), "ms_per_solve": round(msmx, 4),
+                  "ms_per_solve_stats": step_stats(permx),
                   "iterations": infomx["iterations"], "true_rel_residual": infomx["true_rel_residual"],
+                  "rel_l2_vs_fp64_solution": err_mx,
                   "krylov": "flexible CG", "dtype": "f32 cycle / f64 Krylov + coarsest"},
+        "r3x16": small,
+        "r5x64a_adjoint": adjoint,
+        "r7x128": large,
         "vcycle": vc,
         "velocity_pressure": vp,
         "nlo": nlo,
@@ -745,6 +897,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-nlo", action="store_true", help="skip the next-to-lowest-order section")
     ap.add_argument("--no-vp", action="store_true", help="skip the lowest-order velocity-pressure section")
+    ap.add_argument("--no-extra", action="store_true", help="skip the r3x16, r5x64a and r7x128 sections")
+    ap.add_argument("--no-large", action="store_true", help="skip the r7x128 section")
     ap.add_argument("--oracle-iterations", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")

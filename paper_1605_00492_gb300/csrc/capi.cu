@@ -85,6 +85,9 @@ void release(hmg_ctx* c) {
   c->host_sc = nullptr;
   if (c->gm_host) cudaFreeHost(c->gm_host);
   c->gm_host = nullptr;
+  if (c->cg_loop_host) cudaFreeHost(c->cg_loop_host);
+  c->cg_loop_host = nullptr;
+  c->cg_loop = nullptr;   // device memory: freed with the allocations
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   c->ev0 = c->ev1 = nullptr;
@@ -319,7 +322,7 @@ bool fused_beta(const hmg_ctx* c, const CycleCfg& cfg) {
   return !cfg.mixed && (cfg.nlev > 1 || cfg.n_coarse > 1);
 }
 
-void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
+void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s, bool read_back = true) {
   Level& L = c->lv[0];
   if (fused_beta(c, cfg)) {
     SweepDot d = beta_dot(c, flexible);
@@ -334,8 +337,9 @@ void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t
   Reduce ra = red_with(c, EPI_ALPHA);
   LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s));
   LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
-  cuda_ok(cudaMemcpyAsync(c->host_sc, c->red.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s),
-          "scalar read");
+  if (read_back)
+    cuda_ok(cudaMemcpyAsync(c->host_sc, c->red.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s),
+            "scalar read");
 }
 
 // Graph keys: the cycle configuration, the Krylov method and, for GMRES, the
@@ -407,6 +411,84 @@ void harvest_body(hmg_ctx* c, const hmg_ctx::BodyGraph* g) {
   }
 }
 
+// The CG iterations after the first as one CUDA graph: a stopping-test
+// kernel (k_cg_control), then a while node whose body is one iteration
+// followed by the same test, so the whole loop runs without the host.  The
+// test sets the node's condition; it ends the loop at max_iter at the
+// latest, so the graph always terminates.  Graphs with a conditional node
+// cannot hold event nodes, so traced solves take the host-side loop.
+hmg_ctx::BodyGraph* run_loop(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s) {
+  const int64_t key = graph_key(cfg, flexible) + (int64_t(1) << 60);
+  hmg_ctx::BodyGraph* g = nullptr;
+  for (auto& bg : c->graphs)
+    if (bg.key == key && bg.trace == 0) g = &bg;
+  if (!g) {
+    if (!c->cg_loop) c->cg_loop = dalloc<CgLoop>(c, 1);
+    cudaStream_t cs = c->capture_stream;
+    cudaGraph_t graph = nullptr;
+    cuda_ok(cudaGraphCreate(&graph, 0), "graph create");
+    int body_kernels = 0;
+    try {
+      cudaGraphConditionalHandle hnd;
+      cuda_ok(cudaGraphConditionalHandleCreate(&hnd, graph, 0, cudaGraphCondAssignDefault), "conditional handle");
+      cuda_ok(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+              "begin capture");
+      launch_cg_control(c->cg_loop, c->red.sc, hnd, cs);
+      cudaError_t le = cudaGetLastError();
+      cudaGraph_t same = nullptr;
+      cuda_ok(cudaStreamEndCapture(cs, &same), "end capture");
+      cuda_ok(le, "k_cg_control");
+      cudaGraphNode_t first = nullptr;
+      size_t nn = 1;
+      cuda_ok(cudaGraphGetNodes(graph, &first, &nn), "graph nodes");
+      if (nn != 1) throw Fail{HMG_ERR_CUDA, "loop graph: unexpected node count"};
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hnd;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t wnode = nullptr;
+      cuda_ok(cudaGraphAddNode(&wnode, graph, &first, nullptr, 1, &np), "while node");
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      const int64_t before = c->launches;
+      cuda_ok(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+              "begin capture");
+      c->capturing = true;
+      try {
+        iteration_body(c, cfg, flexible, cs, false);
+        launch_cg_control(c->cg_loop, c->red.sc, hnd, cs);
+        launched("k_cg_control");
+        c->launches += 1;
+      } catch (...) {
+        c->capturing = false;
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(cs, &dummy);
+        c->launches = before;
+        throw;
+      }
+      c->capturing = false;
+      body_kernels = (int)(c->launches - before);
+      c->launches = before;
+      cudaGraph_t body_same = nullptr;
+      cuda_ok(cudaStreamEndCapture(cs, &body_same), "end capture");
+    } catch (...) {
+      cudaGraphDestroy(graph);
+      throw;
+    }
+    hmg_ctx::BodyGraph bg;
+    bg.key = key;
+    bg.trace = 0;
+    bg.kernels = body_kernels;
+    cudaError_t e = cudaGraphInstantiate(&bg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cuda_ok(e, "graph instantiate");
+    c->graphs.push_back(std::move(bg));
+    g = &c->graphs.back();
+  }
+  cuda_ok(cudaGraphLaunch(g->exec, s), "graph launch");
+  return g;
+}
+
 hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* info, cudaStream_t s);
 
 // The solve on the tiled vectors kb (right-hand side) and kx (solution).
@@ -431,6 +513,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     throw Fail{HMG_ERR_NONFINITE, "right-hand side is not finite"};
   }
   hmg_status st = HMG_ERR_NOT_CONVERGED;
+  hmg_ctx::BodyGraph* loop_graph = nullptr;   // set when the device-side loop ran
   if (bb == 0.0) {
     inf.converged = 1;
     st = HMG_OK;
@@ -449,31 +532,44 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     Reduce ra = red_with(c, EPI_ALPHA);
     LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s));
     LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
-    read_scalars(c, s);
     const double stop2 = p.rtol * p.rtol * bb;
-    for (int k = 1;; ++k) {
-      inf.iterations = k;
-      const int flag = (int)c->host_sc[S_FLAG];
-      const double rr = c->host_sc[S_RR];
-      inf.rel_residual = std::sqrt(rr / bb);
-      c->history.push_back(inf.rel_residual);
-      if (flag & F_NONFINITE) {
-        st = HMG_ERR_NONFINITE;
-        break;
+    if (!c->prof_on && p.max_iter <= CG_LOOP_HIST) {
+      // device-side loop: one graph launch; its state is read with the
+      // true residual's scalars at the end
+      if (!c->cg_loop_host)
+        cuda_ok(cudaHostAlloc((void**)&c->cg_loop_host, sizeof(CgLoop), cudaHostAllocDefault), "host alloc");
+      if (!c->cg_loop) c->cg_loop = dalloc<CgLoop>(c, 1);
+      launch_cg_loop_init(c->cg_loop, p.rtol * p.rtol, p.max_iter, s);
+      launched("k_cg_loop_init");
+      c->launches += 1;
+      loop_graph = run_loop(c, cfg, flexible, s);
+      cuda_ok(cudaMemcpyAsync(c->cg_loop_host, c->cg_loop, sizeof(CgLoop), cudaMemcpyDeviceToHost, s), "loop read");
+    } else {
+      read_scalars(c, s);
+      for (int k = 1;; ++k) {
+        inf.iterations = k;
+        const int flag = (int)c->host_sc[S_FLAG];
+        const double rr = c->host_sc[S_RR];
+        inf.rel_residual = std::sqrt(rr / bb);
+        c->history.push_back(inf.rel_residual);
+        if (flag & F_NONFINITE) {
+          st = HMG_ERR_NONFINITE;
+          break;
+        }
+        if (flag & F_BREAKDOWN) {
+          st = HMG_ERR_BREAKDOWN;
+          break;
+        }
+        if (rr < stop2) {
+          inf.converged = 1;
+          st = HMG_OK;
+          break;
+        }
+        if (k == p.max_iter) break;
+        hmg_ctx::BodyGraph* g = run_body(c, cfg, flexible, s);
+        cuda_ok(cudaStreamSynchronize(s), "solve");
+        harvest_body(c, g);
       }
-      if (flag & F_BREAKDOWN) {
-        st = HMG_ERR_BREAKDOWN;
-        break;
-      }
-      if (rr < stop2) {
-        inf.converged = 1;
-        st = HMG_OK;
-        break;
-      }
-      if (k == p.max_iter) break;
-      hmg_ctx::BodyGraph* g = run_body(c, cfg, flexible, s);
-      cuda_ok(cudaStreamSynchronize(s), "solve");
-      harvest_body(c, g);
     }
   }
   // true residual ||b - H^ x|| / ||b||
@@ -481,6 +577,21 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   LAUNCH(c, HMG_K_RESID_SQ, 0, s, launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s));
   cuda_ok(cudaEventRecord(c->ev1, s), "event");
   read_scalars(c, s);
+  if (loop_graph) {
+    const CgLoop& lh = *c->cg_loop_host;
+    const int k = lh.k;
+    if (k < 1 || k > p.max_iter) throw Fail{HMG_ERR_CUDA, "device loop returned an invalid iteration count"};
+    c->launches += 1 + (int64_t)(k - 1) * loop_graph->kernels;
+    inf.iterations = k;
+    c->history.assign(lh.hist, lh.hist + k);
+    inf.rel_residual = c->history.back();
+    if (lh.flag & F_NONFINITE) st = HMG_ERR_NONFINITE;
+    else if (lh.flag & F_BREAKDOWN) st = HMG_ERR_BREAKDOWN;
+    else if (lh.rr < p.rtol * p.rtol * bb) {
+      inf.converged = 1;
+      st = HMG_OK;
+    }
+  }
   inf.true_rel_residual = bb > 0 ? std::sqrt(c->host_sc[S_TRUE] / bb) : 0.0;
   float ms = 0.f;
   cuda_ok(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event time");

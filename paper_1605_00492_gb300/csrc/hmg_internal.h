@@ -270,6 +270,20 @@ void launch_transpose64(bool to_tiled, int nitems, int nz, int nzc, const double
 void launch_dot(const Level& L, const double* a, const double* b, const double* c, const double* d,
                 const Reduce& red, cudaStream_t s);  // s0 = a.b, s1 = c.d (c may be null)
 void launch_update_p(const Level& L, double* p, const double* z, const double* sc, cudaStream_t s);
+// Device-side CG loop state: the iteration k, its limit, rtol^2 and the
+// relative residual after each iteration (at most CG_LOOP_HIST iterations;
+// longer solves run the host-side loop).
+constexpr int CG_LOOP_HIST = 1024;
+struct CgLoop {
+  double rtol2;
+  double rr;          // ||r_k||^2 and the reduction flags seen by the last test
+  int flag;
+  int max_iter;
+  int k;
+  double hist[CG_LOOP_HIST];
+};
+void launch_cg_loop_init(CgLoop* loop, double rtol2, int max_iter, cudaStream_t s);
+void launch_cg_control(CgLoop* loop, const double* sc, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_update_xr(const Level& L, double* x, double* r, const double* p, const double* q,
                       const Reduce& red, cudaStream_t s);
 void launch_resid_sq(const Level& L, const double* b, const double* q, const Reduce& red,
@@ -400,6 +414,10 @@ struct hmg_ctx {
   hmg::GsWork gm{};
   double* gm_y = nullptr;
   double* gm_host = nullptr;      // page-locked copy of gm_small
+  // device-side CG loop: its state (device, through the context's allocator)
+  // and a page-locked copy read once after the loop
+  hmg::CgLoop* cg_loop = nullptr;
+  hmg::CgLoop* cg_loop_host = nullptr;
 
   hmg::MixedSys mx;               // velocity-pressure system, set up by its first use
   hmg::NloSys nlo;                // next-to-lowest-order system, set up by its first use

@@ -228,4 +228,39 @@ void launch_check_finite(const Level& L, const double* v, const Reduce& red, cud
   k_dot<1><<<reduce_grid(L.Np), 256, 0, s>>>(L.Np, v, v, nullptr, nullptr, red);
 }
 
+// Stopping test of the device-side CG loop (the body of a CUDA-graph while
+// node).  It runs after the update of x and r of iteration k = loop->k, once,
+// on one thread: it stores ||r_k|| / ||b|| in the history and ends the loop
+// (condition 0) on a non-finite value or a breakdown flag, on
+// ||r_k||^2 < rtol^2 ||b||^2, or at k = max_iter; otherwise it advances k.
+// The same test, in the same FP64 operations, as the host-side loop.
+__global__ void k_cg_control(CgLoop* loop, const double* __restrict__ sc, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = loop->k;
+  const double rr = sc[S_RR], bb = sc[S_BB];
+  const int flag = (int)sc[S_FLAG];
+  if (k >= 1 && k <= CG_LOOP_HIST) loop->hist[k - 1] = sqrt(rr / bb);
+  const bool stop = (flag & (F_NONFINITE | F_BREAKDOWN)) || rr < loop->rtol2 * bb || k >= loop->max_iter ||
+                    k >= CG_LOOP_HIST;
+  loop->rr = rr;
+  loop->flag = flag;
+  if (!stop) loop->k = k + 1;
+  cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+__global__ void k_cg_loop_init(CgLoop* loop, double rtol2, int max_iter) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  loop->rtol2 = rtol2;
+  loop->max_iter = max_iter;
+  loop->k = 1;
+}
+
+void launch_cg_control(CgLoop* loop, const double* sc, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_cg_control<<<1, 32, 0, s>>>(loop, sc, h);
+}
+
+void launch_cg_loop_init(CgLoop* loop, double rtol2, int max_iter, cudaStream_t s) {
+  k_cg_loop_init<<<1, 32, 0, s>>>(loop, rtol2, max_iter);
+}
+
 }  // namespace hmg

@@ -30,9 +30,12 @@ DEV = "cuda:0"
 
 
 class Full:
-    def __init__(self, name, theta=False):
-        w = gi.WORKLOADS[name]
-        self.r, self.nz, self.L = w["refinement"], w["nlayers"], w["nlevels"]
+    def __init__(self, name, theta=False, shape=None):
+        if shape is None:
+            w = gi.WORKLOADS[name]
+            self.r, self.nz, self.L = w["refinement"], w["nlayers"], w["nlevels"]
+        else:
+            self.r, self.nz, self.L = shape
         self.ms = mesh.hierarchy(self.r, self.L)
         self.prm = helmholtz.Params(refinement=self.r, nlayers=self.nz)
         n = self.ms[0].ncols * self.nz
@@ -90,6 +93,35 @@ def test_r6x64_manufactured_solution(r6):
     x, info = r6.h.solve(r6.gpu(b), rtol=1e-10)
     assert info["converged"] == 1
     assert rel_l2(r6.host(x), ps[r6.idx]) < 1e-6
+
+
+def test_r5x128_parity_at_128_layers():
+    """128 layers per column, as in the r7x128 workload, compared with the
+    oracle: refinement 5 (20,480 columns, 640 tiles of 32) x 128 layers
+    (2.6 M cells), 5 levels.  The finest level takes the same kernels as
+    r7x128's: the FP64 tile sweep with its 66 KB of shared memory (opt-in
+    above 48 KB) and, in the mixed form, the FP32 tile sweep (the register
+    sweep has no 128-layer variant); level 1 (160 tiles) the staged FP32
+    sweep with 115 KB.  Operator at 1e-13, FP64 V-cycle at 1e-12, the mixed
+    V-cycle's error against the FP64 oracle V-cycle (bound 1e-5), the FP64 solve at 1e-9 with the iteration count within 1, and the
+    mixed solve against the oracle's FP64 solution (bound 1e-6)."""
+    f = Full(None, shape=(5, 128, 5))
+    n = f.ops[0].ncells
+    x = gi.rhs(n, seed=7)
+    assert rel_l2(f.host(f.h.apply(f.gpu(x))), (f.ops[0].H @ x)[f.idx]) < 1e-13
+    b = gi.rhs(n)
+    z_ref = multigrid.vcycle(f.ops, b)
+    assert rel_l2(f.host(f.h.vcycle(f.gpu(b))), z_ref[f.idx]) < 1e-12
+    zm = f.h.vcycle(f.gpu(b), precision="mixed")
+    assert rel_l2(f.host(zm), z_ref[f.idx]) < 1e-5
+    x_ref, info_ref = krylov.pcg(f.ops[0].H.dot, lambda v: multigrid.vcycle(f.ops, v), b, rtol=1e-8)
+    xg, info = f.h.solve(f.gpu(b), rtol=1e-8)
+    assert info["converged"] == 1 and abs(info["iterations"] - info_ref.iterations) <= 1
+    assert rel_l2(f.host(xg), x_ref[f.idx]) <= 1e-9
+    xm, infom = f.h.solve(f.gpu(b), precision="mixed", rtol=1e-8)
+    assert infom["converged"] == 1 and infom["true_rel_residual"] < 2e-8
+    assert rel_l2(f.host(xm), x_ref[f.idx]) < 1e-6
+    f.h.close()
 
 
 def test_r5x64_adjoint_gradients():
