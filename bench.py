@@ -46,6 +46,16 @@ def workload_desc(name):
                         "2 coarsest sweeps, GMRES(30) to 1e-5")
     return shell + (f"{w['nlevels']} levels, nu_CFL = 8, omega = 0.8, "
                     "2 pre / 2 post sweeps, 2 coarsest sweeps, PCG to 1e-8")
+def bench_config(name):
+    """The config dict of the JSON line (the same for both arms)."""
+    import hmg_inputs as gi
+    w = gi.WORKLOADS[name]
+    return {"workload": f"{name}: {workload_desc(name)}", "ncols": gi.ncolumns(w["refinement"]),
+            "nlayers": w["nlayers"], "ncells": gi.ncells(w["refinement"], w["nlayers"]), "nlevels": w["nlevels"],
+            "rhs": "N(0,1) per cell, seed 0", "krylov": "CG",
+            "l2": "working set > 1 GB, larger than the 126 MB L2: no flush"}
+
+
 # PCG iterations of the full FP64 solve of this workload (oracle and GPU agree;
 # asserted by tests/test_gpu_fullsize.py).  Used to scale the oracle sample.
 ORACLE_ITERATIONS = 11
@@ -725,9 +735,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms64, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {workload_desc(args.workload)}", "ncols": h.levels[0]["ncols"], "nlayers": nz,
-                   "ncells": n, "nlevels": L, "rhs": "N(0,1) per cell, seed 0", "krylov": "CG",
-                   "l2": "working set > 1 GB, larger than the 126 MB L2: no flush"},
+        "config": bench_config(args.workload),
         "ms_per_step_stats": step_stats(per64),
         "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
         "setup": setup,
@@ -878,7 +886,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{args.workload}: {workload_desc(args.workload)}"},
+           "config": bench_config(args.workload),
            "seconds_per_pcg_iteration": round(iter_s, 4),
            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},

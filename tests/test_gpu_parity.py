@@ -400,3 +400,40 @@ def test_algorithmic_experiments_small():
     hist = experiments.history(refinement=3, nlayers=16, nlevels=3)
     mg = hist["multigrid"]
     assert mg[-1] < 1e-8 and all(b < a for a, b in zip(mg, mg[1:]))
+
+
+def test_caller_allocator_backs_the_context_and_solves_match_oracle():
+    """hmg_build_hierarchy_with_allocator with the binding's torch_allocator:
+    every device allocation of the context (levels, Krylov vectors, the CG
+    loop state, the GMRES basis allocated on first use) comes from PyTorch's
+    caching allocator, and the solves agree with the oracle as with the
+    CUDA runtime's allocator (1e-9, iterations within 1)."""
+    r, nz, L = 3, 16, 3
+    ms = mesh.hierarchy(r, L)
+    prm = helmholtz.Params(refinement=r, nlayers=nz)
+    ops = helmholtz.assemble_hierarchy(ms, prm)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    h = hmg.Hierarchy(r, nz, L, allocator=hmg.torch_allocator())
+    h.assemble()
+    after_build = torch.cuda.memory_allocated()
+    assert after_build > before
+    cen, _ = h.export_mesh(0)
+    idx = cell_permutation(column_permutation(cen, ms[0].centroid), nz)
+    b = gi.rhs(ops[0].ncells)
+    bg = torch.tensor(b[idx], dtype=torch.float64, device=DEV)
+    x_ref, info_ref = krylov.pcg(ops[0].H.dot, lambda v: multigrid.vcycle(ops, v), b, rtol=1e-8)
+    used = []
+    for krylov_name in ("cg", "gmres"):
+        x, info = h.solve(bg, krylov=krylov_name, rtol=1e-8)
+        assert info["converged"] == 1
+        assert rel_l2(x.cpu().numpy(), x_ref[idx]) <= 1e-9
+        if krylov_name == "cg":
+            assert abs(info["iterations"] - info_ref.iterations) <= 1
+        del x
+        torch.cuda.synchronize()
+        used.append(torch.cuda.memory_allocated())
+    assert used[1] > used[0] > after_build     # CG loop state, then the GMRES basis, from the same pool
+    h.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() <= before + bg.numel() * 8
