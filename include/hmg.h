@@ -259,6 +259,45 @@ hmg_status hmg_nlo_size(const hmg_ctx* ctx, int64_t* n);
  * 9 * ncols doubles.  Errors: INVALID_ARG. */
 hmg_status hmg_export_vertices(const hmg_ctx* ctx, int level, double* verts);
 
+/* ---- Horizontal domain decomposition (Sec. 5: the paper splits the
+ * horizontal domain over MPI processes, exchanges the halo columns before
+ * each parallel loop and reduces the Krylov dot products over processes).
+ * Parts are contiguous ranges of the hierarchical column order, cut in whole
+ * tiles of 32 columns on the coarsest partitioned level and inherited by the
+ * finer levels (the children 4C..4C+3 of an owned column C are owned by the
+ * same part).  Levels 0 .. nlevels - 2 are partitioned; the coarsest level is
+ * gathered on one part (a one-level hierarchy partitions its only level).
+ * In a part's local numbering, owned column c is c - col_begin, the owned
+ * columns are padded to ncols_padded (a multiple of 32), and ghost i (a
+ * column the part's stencils read but another part owns) is
+ * ncols_padded + i.  Ghosts are ordered by (owner part, global column). */
+typedef struct {
+  int32_t col_begin, col_end; /* owned columns [col_begin, col_end), global numbering of the level */
+  int32_t ncols_padded;       /* col_end - col_begin rounded up to 32: local index of ghost 0 */
+  int32_t n_ghost;            /* ghost columns */
+  int32_t n_send;             /* entries of the send list: owned columns that are ghosts of other parts */
+} hmg_part_info;
+
+/* Host only (no context, no GPU): the partition of the hierarchy of
+ * `refinement` and `nlevels` levels into `nparts` parts, for one part and one
+ * partitioned level.  Errors: INVALID_ARG (bad sizes; nparts larger than the
+ * tiles of the coarsest partitioned level; level not partitioned). */
+hmg_status hmg_partition_info(int refinement, int nlevels, int nparts, int part, int level, hmg_part_info* out);
+
+/* Host only: the tables of that part and level, into caller-owned host
+ * buffers (sizes from hmg_partition_info; any pointer may be NULL):
+ *   ghost_col[n_ghost]          global column of each ghost
+ *   ghost_owner[n_ghost]        the part that owns it
+ *   ghost_owner_local[n_ghost]  its local index in the owner
+ *   local_nbr[3 n_own]          the three neighbours of each owned column, local indices
+ *   send_col[n_send], send_to[n_send]: the owned columns other parts read, grouped by
+ *                               the receiving part and, within a group, in that part's
+ *                               ghost order (so a receiver unpacks its halo in order).
+ * Errors: as hmg_partition_info. */
+hmg_status hmg_partition_tables(int refinement, int nlevels, int nparts, int part, int level, int32_t* ghost_col,
+                                int32_t* ghost_owner, int32_t* ghost_owner_local, int32_t* local_nbr,
+                                int32_t* send_col, int32_t* send_to);
+
 /* Host-only assembly of the NLO operator on the finest mesh of `mesh` (no
  * context, no GPU): diag[36 (c nlayers + l) + 6 u + u'] = H^[(c,l,u),(c,l,u')],
  * sub[36 (c nlayers + l) + 6 u + u'] = H^[(c,l,u),(c,l-1,u')] (zero for l = 0),
@@ -396,7 +435,9 @@ typedef enum {
   HMG_K_NLO_RESID = 14,      /* NLO b_c = P^T (b - H^ u) into the lowest-order level */
   HMG_K_NLO_APPLY = 15,      /* NLO H^ x */
   HMG_K_NLO_SWEEP0 = 16,     /* NLO first column block relaxation from u = 0 */
-  HMG_K_COUNT = 17
+  HMG_K_COARSE = 17,         /* the coarse end of the V-cycle as one cooperative kernel
+                                (level = its first level) */
+  HMG_K_COUNT = 18
 } hmg_kernel_id;
 
 typedef struct {
@@ -405,6 +446,16 @@ typedef struct {
   int launches;
   double total_ms;  /* sum of CUDA-event durations of those launches */
 } hmg_kernel_stat;
+
+/* Whether V-cycles run their coarse end (Algorithm 1 from the first level
+ * below the finest with at most 160 tiles of 32 columns, down to the
+ * coarsest and back) as one cooperative kernel with a grid-wide barrier
+ * between its sweep and residual passes (enable != 0, the default), or as
+ * one kernel per pass.  Both run the same arithmetic in the same order and
+ * give identical results; the fused form saves the launch and memory
+ * latency of the small levels.  Applies to later calls on this context.
+ * Errors: INVALID_ARG (ctx NULL). */
+hmg_status hmg_set_coarse_fusion(hmg_ctx* ctx, int enable);
 
 /* Tracing (the per-level kernel breakdown of Sec. 5.4): from this call on,
  * every launch of a kernel class whose bit is set in kernel_mask, on a level

@@ -68,7 +68,12 @@ class KernelStat(ctypes.Structure):
 
 KERNELS = ["sweep0", "sweep", "prolong", "resid_restrict", "apply", "dot", "update_xr", "update_p", "layout",
            "resid_sq", "assembly", "theta_grad", "ortho", "nlo_sweep", "nlo_resid", "nlo_apply",
-           "nlo_sweep0"]
+           "nlo_sweep0", "coarse_cycle"]
+
+
+class PartInfo(ctypes.Structure):
+    _fields_ = [("col_begin", ctypes.c_int32), ("col_end", ctypes.c_int32), ("ncols_padded", ctypes.c_int32),
+                ("n_ghost", ctypes.c_int32), ("n_send", ctypes.c_int32)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -115,6 +120,9 @@ _SIGNATURES = {
     "hmg_sync": [_P, _P],
     "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
     "hmg_convert_fp32_to_fp64": [_P, _P, ctypes.c_int64, _P],
+    "hmg_set_coarse_fusion": [_P, _I],
+    "hmg_partition_info": [_I, _I, _I, _I, _I, ctypes.POINTER(PartInfo)],
+    "hmg_partition_tables": [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P],
     "hmg_profile_start": [_P, ctypes.c_uint, ctypes.c_uint],
     "hmg_profile_stop": [_P, ctypes.POINTER(KernelStat), _I, ctypes.POINTER(_I)],
     "hmg_launch_count": [_P, ctypes.POINTER(ctypes.c_int64)],
@@ -436,6 +444,11 @@ class Hierarchy:
                                            _ptr(out), _stream(stream)))
         return out
 
+    def set_coarse_fusion(self, enable):
+        """Run the coarse end of each V-cycle as one cooperative kernel (True,
+        the default) or as one kernel per pass (False); same results."""
+        self._check(self.lib.hmg_set_coarse_fusion(self._ctx, 1 if enable else 0))
+
     def profile_start(self, kernels=None, levels=None):
         """Bracket launches of the named kernel classes on the given levels with
         CUDA events (all when None)."""
@@ -469,6 +482,32 @@ class Hierarchy:
 
     def sync(self, stream=None):
         self._check(self.lib.hmg_sync(self._ctx, _stream(stream)))
+
+
+def partition_tables(refinement, nlevels, nparts, part, level):
+    """Host-only (no GPU): the horizontal domain decomposition of the column
+    hierarchy for one part and one partitioned level (include/hmg.h,
+    hmg_partition_tables).  Returns a dict: col_begin, col_end, ncols_padded
+    and the int32 arrays ghost_col, ghost_owner, ghost_owner_local, local_nbr
+    (n_own, 3), send_col, send_to."""
+    import numpy as np
+    lib = load_library()
+    info = PartInfo()
+    st = lib.hmg_partition_info(refinement, nlevels, nparts, part, level, ctypes.byref(info))
+    if st != 0:
+        raise HMGError(st, lib.hmg_last_error(None).decode())
+    n_own = info.col_end - info.col_begin
+    out = dict(col_begin=info.col_begin, col_end=info.col_end, ncols_padded=info.ncols_padded,
+               ghost_col=np.zeros(info.n_ghost, np.int32), ghost_owner=np.zeros(info.n_ghost, np.int32),
+               ghost_owner_local=np.zeros(info.n_ghost, np.int32), local_nbr=np.zeros((n_own, 3), np.int32),
+               send_col=np.zeros(info.n_send, np.int32), send_to=np.zeros(info.n_send, np.int32))
+    st = lib.hmg_partition_tables(refinement, nlevels, nparts, part, level,
+                                  *(out[k].ctypes.data_as(_P) for k in ("ghost_col", "ghost_owner",
+                                                                         "ghost_owner_local", "local_nbr",
+                                                                         "send_col", "send_to")))
+    if st != 0:
+        raise HMGError(st, lib.hmg_last_error(None).decode())
+    return out
 
 
 def nlo_host_blocks(refinement, nlayers, c=300.0, N=0.01, nu_cfl=8.0, dx_m=0.0, omega=0.8, radius_m=6.371e6,

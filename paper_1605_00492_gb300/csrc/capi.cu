@@ -197,6 +197,7 @@ struct CycleCfg {
   int nu_pre = 2, nu_post = 2, n_coarse = 2;
   int nlev = 1;          // levels used: 0 .. nlev - 1 (nlev = 1: single-level line relaxation)
   bool mixed = false;
+  bool fuse = true;      // coarse end of the cycle as one cooperative kernel
   double omega = 0.8;
 };
 
@@ -208,6 +209,7 @@ CycleCfg make_cfg(const hmg_ctx* c, int nu_pre, int nu_post, int n_coarse, int l
   cfg.nlev = levels > 0 ? levels : (int)c->lv.size();
   cfg.mixed = precision == HMG_PRECISION_MIXED;
   cfg.omega = c->ph.omega;
+  cfg.fuse = c->fuse_coarse;
   return cfg;
 }
 
@@ -219,6 +221,14 @@ int level_dt(const hmg_ctx* c, const CycleCfg& cfg, int lev) {
 void* work(Level& L, int dt, int which) {
   if (dt == HMG_FP64) return which == 0 ? (void*)L.ua64 : (which == 1 ? (void*)L.ub64 : (void*)L.b64);
   return which == 0 ? (void*)L.ua32 : (which == 1 ? (void*)L.ub32 : (void*)L.b32);
+}
+
+// Whether the cycle from level lev down runs as the fused coarse-level
+// kernel: lev is below the finest, has at most CC_MAX_TILES tiles, and the
+// levels from it down fit the kernel's argument block.
+bool fused_from(const hmg_ctx* c, const CycleCfg& cfg, int lev) {
+  return cfg.fuse && lev >= 1 && lev < cfg.nlev && c->lv[lev].ncp / TW <= CC_MAX_TILES &&
+         cfg.nlev - lev <= CC_MAX_LEVELS;
 }
 
 // out <- V_lev b (zero initial guess).  b has type b_dt, out has type out_dt;
@@ -259,7 +269,13 @@ void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, vo
   void* bc = work(C, cdt, 2);
   LAUNCH(c, HMG_K_RESID_RESTRICT, lev, s, launch_resid_restrict(L, dt, bl, cur, bc, cdt, s));
   void* ec = cdt == HMG_FP64 ? (void*)C.ux64 : (void*)C.ux32;
-  cycle(c, cfg, lev + 1, bc, cdt, ec, cdt, s);
+  if (fused_from(c, cfg, lev + 1))
+    LAUNCH(c, HMG_K_COARSE, lev + 1, s,
+           cuda_ok(launch_coarse_cycle(c->lv.data(), lev + 1, nlev, cfg.nu_pre, cfg.nu_post, cfg.n_coarse,
+                                       cfg.omega, cfg.mixed, bc, ec, s),
+                   "coarse cycle"));
+  else
+    cycle(c, cfg, lev + 1, bc, cdt, ec, cdt, s);
   // post-smoothing; the coarse correction is added by its own pass first on
   // large FP64 levels (1 instead of 4 FP64 operations per cell) and on small
   // FP32 levels (whose staged sweep takes no fused prolongation), and is
@@ -346,8 +362,8 @@ void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t
 // Arnoldi step j within a restart cycle (its vectors are baked in).
 int64_t graph_key(const CycleCfg& cfg, bool flexible, int gmres_step = -1) {
   const int64_t base =
-      (((((cfg.mixed ? 1 : 0) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 + cfg.nu_post) * 65 + cfg.n_coarse) *
-          33 + cfg.nlev;
+      ((((((cfg.fuse ? 1 : 0) * 2 + (cfg.mixed ? 1 : 0)) * 2 + (flexible ? 1 : 0)) * 65 + cfg.nu_pre) * 65 +
+        cfg.nu_post) * 65 + cfg.n_coarse) * 33 + cfg.nlev;
   return base * (GMRES_MAX_RESTART + 1) + (gmres_step + 1);
 }
 
@@ -1748,8 +1764,56 @@ const char* hmg_kernel_name(int kernel) {
   static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",     "prolong",  "resid_restrict", "apply",
                                            "dot",    "update_xr", "update_p", "layout",         "resid_sq",
                                            "assembly", "theta_grad", "ortho",    "nlo_sweep",      "nlo_resid",
-                                           "nlo_apply", "nlo_sweep0"};
+                                           "nlo_apply", "nlo_sweep0", "coarse_cycle"};
   return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
+}
+
+static const PartLevel& partition_part(int refinement, int nlevels, int nparts, int part, int level,
+                                       PartitionPlan& keep) {
+  require(refinement >= 0 && refinement <= 9, "refinement must be in [0, 9]");
+  require(nlevels >= 1 && nlevels <= refinement + 1, "nlevels must be in [1, refinement + 1]");
+  keep = build_partition_for_mesh(refinement, nlevels, nparts);
+  require(part >= 0 && part < nparts, "part must be in [0, nparts)");
+  require(level >= 0 && level < keep.nlevels, "level is not a partitioned level");
+  return keep.lv[level][part];
+}
+
+hmg_status hmg_partition_info(int refinement, int nlevels, int nparts, int part, int level, hmg_part_info* out) {
+  return guarded(nullptr, [&] {
+    require(out != nullptr, "out must not be NULL");
+    PartitionPlan plan;
+    const PartLevel& pl = partition_part(refinement, nlevels, nparts, part, level, plan);
+    out->col_begin = pl.begin;
+    out->col_end = pl.end;
+    out->ncols_padded = pl.n_own_pad;
+    out->n_ghost = (int32_t)pl.ghost_col.size();
+    out->n_send = (int32_t)pl.send_col.size();
+  });
+}
+
+hmg_status hmg_partition_tables(int refinement, int nlevels, int nparts, int part, int level, int32_t* ghost_col,
+                                int32_t* ghost_owner, int32_t* ghost_owner_local, int32_t* local_nbr,
+                                int32_t* send_col, int32_t* send_to) {
+  return guarded(nullptr, [&] {
+    PartitionPlan plan;
+    const PartLevel& pl = partition_part(refinement, nlevels, nparts, part, level, plan);
+    auto put = [](const std::vector<int32_t>& v, int32_t* dst) {
+      if (dst) std::copy(v.begin(), v.end(), dst);
+    };
+    put(pl.ghost_col, ghost_col);
+    put(pl.ghost_owner, ghost_owner);
+    put(pl.ghost_owner_local, ghost_owner_local);
+    put(pl.local_nbr, local_nbr);
+    put(pl.send_col, send_col);
+    put(pl.send_to, send_to);
+  });
+}
+
+hmg_status hmg_set_coarse_fusion(hmg_ctx* ctx, int enable) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  ctx->fuse_coarse = enable != 0;
+  ctx->err.clear();
+  return HMG_OK;
 }
 
 hmg_status hmg_profile_start(hmg_ctx* ctx, unsigned kernel_mask, unsigned level_mask) {

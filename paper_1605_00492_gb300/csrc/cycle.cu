@@ -19,6 +19,11 @@
 #include "hmg_internal.h"
 #include "reduce.cuh"
 
+#include <cooperative_groups.h>
+#include <type_traits>
+
+namespace cg = cooperative_groups;
+
 namespace hmg {
 
 namespace {
@@ -100,11 +105,15 @@ __device__ __forceinline__ T chain(T* R, const T* LO, int lane, int l0, int step
 
 // DOT = 1: also reduce sum_cells da * u' (the r.z of CG, da = the FP64
 // residual); DOT = 2: and sum_cells u' * dc (the z.q of flexible CG).
+// The sweep of one tile by the whole CTA (NW warps); k_tsweep runs it with
+// tile = blockIdx.x, the fused coarse-level cycle (k_coarse_cycle) for the
+// tiles its CTA owns in each sweep phase.
 template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT, bool TW2>
-__global__ void __launch_bounds__(NW * 32)
-k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restrict__ uo,
-         const TE* __restrict__ ec, float* __restrict__ bcopy, T om1, const double* __restrict__ da,
-         const double* __restrict__ dc, Reduce red) {
+__device__ __forceinline__ void tsweep_tile(const LD<T>& L, const int tile, const TB* __restrict__ b,
+                                            const T* __restrict__ u, TO* __restrict__ uo,
+                                            const TE* __restrict__ ec, float* __restrict__ bcopy, T om1,
+                                            const double* __restrict__ da, const double* __restrict__ dc,
+                                            const Reduce& red) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RB = 4;  // rows per warp per batch: their loads are issued together
   const int nz = L.nz;
@@ -112,7 +121,6 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
   T* R = reinterpret_cast<T*>(smem_raw);
   T* LOs = R + (nz + 2) * TW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int tile = blockIdx.x;
   const int c = tile * TW + lane;
   const bool valid = c < L.nc;
   const int64_t base = (int64_t)tile * TW * nz + lane;
@@ -187,7 +195,7 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
   __syncthreads();
   if (!TW2) {
     // one chain warp (plain L D L^T: twist row nz - 1), spread over the sub-partitions
-    const int cw = blockIdx.x % NW;
+    const int cw = tile % NW;
     // B
     if (warp == cw) {
       T y = 0;
@@ -256,7 +264,7 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
     __syncthreads();
   } else {
     // two chain warps on different sub-partitions, spread over the CTAs
-    const int cw0 = blockIdx.x % NW, cw1 = (cw0 + 1) % NW;
+    const int cw0 = tile % NW, cw1 = (cw0 + 1) % NW;
     const int m = L.twist;
     T* YT = R + nz * TW;   // y_m-1 and y_m+1 kept unscaled for the twist row
     T* YB = YT + TW;
@@ -351,6 +359,14 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
     // the tile's shared arrays are free now: reuse them as scratch
     grid_reduce<(DOT == 2 ? 2 : 1)>(a0, a1, red, reinterpret_cast<double*>(smem_raw));
   }
+}
+
+template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, int DOT, bool TW2>
+__global__ void __launch_bounds__(NW * 32)
+k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restrict__ uo,
+         const TE* __restrict__ ec, float* __restrict__ bcopy, T om1, const double* __restrict__ da,
+         const double* __restrict__ dc, Reduce red) {
+  tsweep_tile<T, TB, TO, MODE, TE, NW, DOT, TW2>(L, blockIdx.x, b, u, uo, ec, bcopy, om1, da, dc, red);
 }
 
 // ---------------------------------------------------------------- FP32 staged sweep
@@ -627,6 +643,68 @@ __global__ void __launch_bounds__(NW * 32)
 k_tresid_restrict(LD<T> L, int ntiles, int RG, const T* __restrict__ b, const T* __restrict__ u,
                   TC* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
+  if (RG == 0 && (L.nz & 3) == 0) {
+    // Runs of RC = 4 consecutive layers of one tile per step, every load of
+    // the run issued before the arithmetic: four times the bytes in flight
+    // per warp of the one-row loop below (which was bound by memory latency).
+    constexpr int RC = 4;
+    const int nz = L.nz, nch = nz / RC;
+    const int nwt = gridDim.x * NW, gw = blockIdx.x * NW + (threadIdx.x >> 5);
+    const int total = ntiles * nch;
+    const int per = (total + nwt - 1) / nwt;
+    const int i0 = gw * per, i1 = min(total, i0 + per);
+    typename Vec4<T>::type g{};
+    int64_t s0 = 0, s1 = 0, s2 = 0, qc = 0, base = 0;
+    bool valid = false;
+    int cur = -1;
+    for (int it = i0; it < i1; ++it) {
+      const int tile = it / nch, l0 = (it - tile * nch) * RC;
+      if (tile != cur) {
+        cur = tile;
+        const int c = tile * TW + lane;
+        valid = c < L.nc;
+        base = (int64_t)tile * TW * nz + lane;
+        const int4 nb = L.nbr[c];
+        g = L.gh[c];
+        s0 = tile_base(nb.x, nz);
+        s1 = tile_base(nb.y, nz);
+        s2 = tile_base(nb.z, nz);
+        qc = tile_base(c >> 2, nz);
+      }
+      const int64_t t0 = base + (int64_t)l0 * TW, o0 = (int64_t)l0 * TW;
+      T bv[RC], dv[RC], ev[RC + 1], uv[RC + 2], a0[RC], a1[RC], a2[RC];
+#pragma unroll
+      for (int i = 0; i < RC; ++i) {
+        const int64_t t = t0 + i * TW, o = o0 + i * TW;
+        bv[i] = b[t];
+        dv[i] = L.d[t];
+        uv[i + 1] = u[t];
+        a0[i] = u[s0 + o];
+        a1[i] = u[s1 + o];
+        a2[i] = u[s2 + o];
+        ev[i] = (l0 + i > 0) ? L.e[t] : (T)0;
+      }
+      const bool top = l0 + RC < nz;
+      ev[RC] = top ? L.e[t0 + RC * TW] : (T)0;
+      uv[0] = (l0 > 0) ? u[t0 - TW] : (T)0;
+      uv[RC + 1] = top ? u[t0 + RC * TW] : (T)0;
+#pragma unroll
+      for (int i = 0; i < RC; ++i) {
+        // the FMA order of stencil_acc<T, -1>; a missing vertical neighbour
+        // contributes fma(-0, 0, y) = y exactly
+        T r = fma(-dv[i], uv[i + 1], bv[i]);
+        r = fma(-ev[i], uv[i], r);
+        r = fma(-ev[i + 1], uv[i + 2], r);
+        r = fma(g.x, a0[i], r);
+        r = fma(g.y, a1[i], r);
+        r = fma(g.z, a2[i], r);
+        r += __shfl_xor_sync(0xffffffffu, r, 1);
+        r += __shfl_xor_sync(0xffffffffu, r, 2);
+        if ((lane & 3) == 0 && valid) bc[qc + o0 + i * TW] = cvt<TC>(r);
+      }
+    }
+    return;
+  }
   if (RG == 0) {
     const int nz = L.nz;
     typename Vec4<T>::type g{};
@@ -876,6 +954,173 @@ void tsweep(const Level& L, const void* b, const void* u, void* uo, const void* 
     tsweep_dot<T, TB, TO, MODE, TE, NW_SWEEP_SMALL>(L, b, u, uo, ec, bcopy, omega, dot, s);
 }
 
+// ---------------------------------------------------------------- fused coarse levels
+//
+// The coarse end of the V-cycle (Algorithm 1 from level ls down to the
+// coarsest and back) as one cooperative kernel: each sweep, residual and
+// prolongation pass is a phase over the whole grid, and a grid-wide barrier
+// separates phases.  On these levels (at most CC_MAX_TILES tiles) every
+// separate kernel is bound by launch and memory latency; here the phases
+// follow each other without a launch, and the level's data written by one
+// phase is read by the next from L2.  The phases are the same per-tile
+// sweeps (tsweep_tile, twisted two-chain solve) and the same residual
+// stencil as the separate kernels, in the same order, so the result is
+// identical.  Every CTA passes the same sequence of barriers: the phase
+// sequence depends only on the kernel arguments.
+
+struct CoarseArgs {
+  int nlev;                        // levels ls .. ls + nlev - 1, the last the coarsest
+  int nu_pre, nu_post, n_coarse;
+  double om1;                      // 1 - omega
+  LD<double> d[CC_MAX_LEVELS];
+  LD<float> f[CC_MAX_LEVELS];
+  int ntiles[CC_MAX_LEVELS];
+  void* ua[CC_MAX_LEVELS];         // the level's work buffers, of the level's type
+  void* ub[CC_MAX_LEVELS];
+  void* bb[CC_MAX_LEVELS];         // right-hand side (restricted residual) of levels below the first
+  void* ux[CC_MAX_LEVELS];         // result of levels below the first (the coarse correction)
+  const void* b_in;                // right-hand side of the first level
+  void* out;                       // result of the first level
+};
+
+template <typename T> __device__ __forceinline__ const LD<T>& cc_view(const CoarseArgs& a, int k);
+template <> __device__ __forceinline__ const LD<double>& cc_view<double>(const CoarseArgs& a, int k) {
+  return a.d[k];
+}
+template <> __device__ __forceinline__ const LD<float>& cc_view<float>(const CoarseArgs& a, int k) {
+  return a.f[k];
+}
+
+template <typename T, typename TO, int MODE, typename TE, int NW>
+__device__ __forceinline__ void cc_sweep(const CoarseArgs& a, int k, const T* b, const T* u, TO* uo, const TE* ec) {
+  const LD<T>& L = cc_view<T>(a, k);
+  for (int t = blockIdx.x; t < a.ntiles[k]; t += gridDim.x) {
+    tsweep_tile<T, T, TO, MODE, TE, NW, 0, true>(L, t, b, u, uo, ec, nullptr, (T)a.om1, nullptr, nullptr,
+                                                 Reduce{});
+    __syncthreads();   // the next tile reuses the shared arrays
+  }
+}
+
+// b_c = P^T (b - H^ u), one (tile, layer) row per warp step over the grid
+template <typename T, typename TC, int NW>
+__device__ __forceinline__ void cc_resid(const CoarseArgs& a, int k, const T* b, const T* u, TC* bc) {
+  const LD<T>& L = cc_view<T>(a, k);
+  const int lane = threadIdx.x & 31, nz = L.nz;
+  const int rows = a.ntiles[k] * nz;
+  for (int row = blockIdx.x * NW + (threadIdx.x >> 5); row < rows; row += gridDim.x * NW) {
+    const int tile = row / nz, l = row - tile * nz;
+    const int c = tile * TW + lane;
+    const bool valid = c < L.nc;
+    T r = 0;
+    if (valid) {
+      const int4 nb = L.nbr[c];
+      const typename Vec4<T>::type g = L.gh[c];
+      const int64_t t = (int64_t)tile * TW * nz + lane + (int64_t)l * TW;
+      r = stencil_acc<T, -1>(L, u, t, l, b[t], g, tile_base(nb.x, nz), tile_base(nb.y, nz), tile_base(nb.z, nz));
+    }
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    if ((lane & 3) == 0 && valid) bc[tile_base(c >> 2, nz) + (int64_t)l * TW] = cvt<TC>(r);
+  }
+}
+
+template <bool MIXED, int NW>
+__global__ void __launch_bounds__(NW * 32) k_coarse_cycle(const __grid_constant__ CoarseArgs a) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  cg::grid_group grid = cg::this_grid();
+  const int last = a.nlev - 1;
+  T* cur[CC_MAX_LEVELS];
+  T* nxt[CC_MAX_LEVELS];
+  // descent: first relaxation from zero, nu_pre - 1 more, residual restricted
+  for (int k = 0; k < last; ++k) {
+    const T* bk = k == 0 ? (const T*)a.b_in : (const T*)a.bb[k];
+    T* c0 = (T*)a.ua[k];
+    T* c1 = (T*)a.ub[k];
+    cc_sweep<T, T, MODE_ZERO, T, NW>(a, k, bk, nullptr, c0, (const T*)nullptr);
+    grid.sync();
+    for (int i = 1; i < a.nu_pre; ++i) {
+      cc_sweep<T, T, MODE_PLAIN, T, NW>(a, k, bk, c0, c1, (const T*)nullptr);
+      grid.sync();
+      T* tmp = c0;
+      c0 = c1;
+      c1 = tmp;
+    }
+    if (k + 1 == last) cc_resid<T, double, NW>(a, k, bk, c0, (double*)a.bb[k + 1]);
+    else cc_resid<T, T, NW>(a, k, bk, c0, (T*)a.bb[k + 1]);
+    grid.sync();
+    cur[k] = c0;
+    nxt[k] = c1;
+  }
+  // coarsest level (FP64 in both forms): n_coarse relaxations from zero
+  {
+    const double* bk = last == 0 ? (const double*)a.b_in : (const double*)a.bb[last];
+    double* outc = last == 0 ? (double*)a.out : (double*)a.ux[last];
+    double* c0 = (double*)a.ua[last];
+    double* c1 = (double*)a.ub[last];
+    cc_sweep<double, double, MODE_ZERO, double, NW>(a, last, bk, nullptr, a.n_coarse == 1 ? outc : c0,
+                                                    (const double*)nullptr);
+    for (int i = 1; i < a.n_coarse; ++i) {
+      grid.sync();
+      cc_sweep<double, double, MODE_PLAIN, double, NW>(a, last, bk, c0, i == a.n_coarse - 1 ? outc : c1,
+                                                       (const double*)nullptr);
+      double* tmp = c0;
+      c0 = c1;
+      c1 = tmp;
+    }
+  }
+  // ascent: the first post-relaxation adds the prolonged correction (u + P e_c)
+  for (int k = last - 1; k >= 0; --k) {
+    grid.sync();
+    const T* bk = k == 0 ? (const T*)a.b_in : (const T*)a.bb[k];
+    T* outk = k == 0 ? (T*)a.out : (T*)a.ux[k];
+    T* c0 = cur[k];
+    T* c1 = nxt[k];
+    for (int i = 0; i < a.nu_post; ++i) {
+      const bool lst = i == a.nu_post - 1;
+      T* dst = lst ? outk : c1;
+      if (i == 0 && k + 1 == last)
+        cc_sweep<T, T, MODE_PRO, double, NW>(a, k, bk, c0, dst, (const double*)a.ux[k + 1]);
+      else if (i == 0)
+        cc_sweep<T, T, MODE_PRO, T, NW>(a, k, bk, c0, dst, (const T*)a.ux[k + 1]);
+      else
+        cc_sweep<T, T, MODE_PLAIN, T, NW>(a, k, bk, c0, dst, (const T*)nullptr);
+      if (!lst) {
+        grid.sync();
+        T* tmp = c0;
+        c0 = c1;
+        c1 = tmp;
+      }
+    }
+  }
+}
+
+template <bool MIXED>
+cudaError_t coarse_cycle_launch(const CoarseArgs& a, size_t smem, cudaStream_t s) {
+  constexpr int NW = NW_SWEEP_SMALL;
+  auto kern = k_coarse_cycle<MIXED, NW>;
+  static SmemOptIn opt_in;
+  cudaError_t e = allow_smem(kern, smem, opt_in);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+  if (!coop) return cudaErrorNotSupported;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(per_sm * sms));
+  cfg.blockDim = dim3(NW * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 }  // namespace
 
 void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, float* bcopy, double omega,
@@ -997,6 +1242,36 @@ void launch_apply(const Level& L, int dt, const void* x, void* y, const Reduce* 
       k<<<HMG_PAR_GRID(k, pc), NW_PAR * 32, 0, s>>>(view<float>(L), nt, rg, (const float*)x, (float*)y, r);
     }
   }
+}
+
+
+cudaError_t launch_coarse_cycle(const Level* lv, int ls, int nlev, int nu_pre, int nu_post, int n_coarse,
+                                double omega, bool mixed, const void* b_in, void* out, cudaStream_t s) {
+  const int n = nlev - ls;
+  if (n < 1 || n > CC_MAX_LEVELS) return cudaErrorInvalidValue;
+  CoarseArgs a{};
+  a.nlev = n;
+  a.nu_pre = nu_pre;
+  a.nu_post = nu_post;
+  a.n_coarse = n_coarse;
+  a.om1 = 1.0 - omega;
+  a.b_in = b_in;
+  a.out = out;
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    const Level& L = lv[ls + k];
+    const bool f32 = mixed && k < n - 1;
+    a.d[k] = view<double>(L);
+    if (f32) a.f[k] = view<float>(L);
+    a.ntiles[k] = ntiles_of(L);
+    a.ua[k] = f32 ? (void*)L.ua32 : (void*)L.ua64;
+    a.ub[k] = f32 ? (void*)L.ub32 : (void*)L.ub64;
+    a.bb[k] = f32 ? (void*)L.b32 : (void*)L.b64;
+    a.ux[k] = f32 ? (void*)L.ux32 : (void*)L.ux64;
+    const size_t sm = (2 * (size_t)L.nz + 2) * TW * (f32 ? sizeof(float) : sizeof(double));
+    if (sm > smem) smem = sm;
+  }
+  return mixed ? coarse_cycle_launch<true>(a, smem, s) : coarse_cycle_launch<false>(a, smem, s);
 }
 
 }  // namespace hmg

@@ -28,6 +28,10 @@ namespace hmg {
 constexpr int TW = 32;                 // columns per tile
 constexpr int SMALL_LEVEL_TILES = 152;  // levels with at most this many tiles are latency bound
 constexpr int FUSED_PROLONG_MAX_TILES = 160;  // FP64 levels up to this size fuse prolongation into the sweep
+// The coarse end of the V-cycle, from the first level of at most
+// CC_MAX_TILES tiles (below the finest) down, runs as one cooperative kernel.
+constexpr int CC_MAX_TILES = 160;
+constexpr int CC_MAX_LEVELS = 8;
 constexpr int RED_MAX_BLOCKS = 16384;  // partial sums of one reduction (>= tiles of the finest level)
 constexpr int GMRES_MAX_RESTART = HMG_GMRES_MAX_RESTART;
 constexpr int GS_MAX_BLOCKS = 1216;    // blocks of one Gram-Schmidt pass (8 per SM)
@@ -41,6 +45,28 @@ struct HostLevel {
 };
 
 std::vector<HostLevel> build_mesh_hierarchy(int refinement, int nlevels);
+
+// Horizontal domain decomposition (partition.cpp).  One part of one
+// partitioned level: owned columns [begin, end) in the global numbering;
+// local numbering = owned columns (c - begin), padded to n_own_pad, then the
+// ghost columns in ghost order, sorted by (owner part, global column).
+struct PartLevel {
+  int32_t begin = 0, end = 0, n_own = 0, n_own_pad = 0;
+  std::vector<int32_t> ghost_col, ghost_owner, ghost_owner_local;
+  std::vector<int32_t> local_nbr;            // n_own * 3 local indices
+  std::vector<int32_t> send_col, send_to;    // sorted by (to, position in the receiver's ghost list)
+};
+struct PartitionPlan {
+  int nparts = 0;
+  int nlevels = 0;                           // partitioned levels 0 .. nlevels - 1
+  std::vector<std::vector<PartLevel>> lv;    // [level][part]
+};
+// Levels split over the parts: all but the coarsest (gathered on one part),
+// or the only one.
+int partitioned_levels(int nlevels);
+PartitionPlan build_partition(const std::vector<std::vector<int32_t>>& nbr, const std::vector<int>& ncols,
+                              int nparts);
+PartitionPlan build_partition_for_mesh(int refinement, int nlevels, int nparts);
 
 struct Level {
   int refinement = 0, nc = 0, ncp = 0, nz = 0;
@@ -258,6 +284,11 @@ struct SweepDot {
 void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo, int uo_dt, const void* ec,
                   int ec_dt, double omega, const SweepDot* dot, cudaStream_t s);
 void launch_prolong(const Level& L, int dt, void* u, const void* ec, int ec_dt, cudaStream_t s);
+// The V-cycle from level ls (b_in: its right-hand side, out: its result,
+// both of its type) down to level nlev - 1 and back, as one cooperative
+// kernel (cycle.cu, k_coarse_cycle).  Returns the launch's error.
+cudaError_t launch_coarse_cycle(const Level* lv, int ls, int nlev, int nu_pre, int nu_post, int n_coarse,
+                                double omega, bool mixed, const void* b_in, void* out, cudaStream_t s);
 void launch_resid_restrict(const Level& L, int dt, const void* b, const void* u, void* bc, int bc_dt,
                            cudaStream_t s);
 void launch_apply(const Level& L, int dt, const void* x, void* y, const Reduce* red, cudaStream_t s);
@@ -372,6 +403,7 @@ struct hmg_ctx {
   hmg::Phys ph{};
   bool assembled = false;
   bool has_theta = false;
+  bool fuse_coarse = true;        // hmg_set_coarse_fusion
   std::vector<hmg::Level> lv;
   // Krylov vectors on the finest level (tiled) and a column-layout staging buffer
   double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr, *kb = nullptr;
