@@ -298,6 +298,26 @@ hmg_status hmg_partition_tables(int refinement, int nlevels, int nparts, int par
                                 int32_t* ghost_owner, int32_t* ghost_owner_local, int32_t* local_nbr,
                                 int32_t* send_col, int32_t* send_to);
 
+/* Run this context as `nparts` parts of the horizontal domain decomposition
+ * above, emulated on its one device (nparts = 1: unpartitioned, the
+ * default).  From then on every V-cycle (hmg_vcycle, and the preconditioner
+ * of hmg_solve in every Krylov method and precision) and every level-0 FP64
+ * operator application (hmg_apply, and the solves' operator) runs as the
+ * parts would on `nparts` devices: each sweep, residual and prolongation
+ * pass once per part on its owned columns, every pass that reads neighbour
+ * columns after a halo exchange (each part packs its send list, the
+ * (sender, receiver) segments are moved, each part unpacks its ghosts), the
+ * coarsest level gathered from the parts, solved once and scattered back,
+ * and the solves' dot products reduced over all parts.  The per-cell
+ * arithmetic is that of the unpartitioned context, so results agree with it
+ * (V-cycles to rounding, solves to the Krylov tolerance).  The velocity-
+ * pressure and NLO systems keep their unpartitioned outer operators.
+ * Allocates each part's local vectors (owned and ghost columns) and tables
+ * through the context's allocator; drops the context's captured graphs.
+ * Errors: INVALID_ARG (nparts outside [1, 16] or above the tiles of the
+ * coarsest partitioned level), OOM, CUDA. */
+hmg_status hmg_partition(hmg_ctx* ctx, int nparts);
+
 /* Host-only assembly of the NLO operator on the finest mesh of `mesh` (no
  * context, no GPU): diag[36 (c nlayers + l) + 6 u + u'] = H^[(c,l,u),(c,l,u')],
  * sub[36 (c nlayers + l) + 6 u + u'] = H^[(c,l,u),(c,l-1,u')] (zero for l = 0),
@@ -437,7 +457,8 @@ typedef enum {
   HMG_K_NLO_SWEEP0 = 16,     /* NLO first column block relaxation from u = 0 */
   HMG_K_COARSE = 17,         /* the coarse end of the V-cycle as one cooperative kernel
                                 (level = its first level) */
-  HMG_K_COUNT = 18
+  HMG_K_HALO = 18,           /* domain decomposition: halo pack / unpack, coarsest-level gather and scatter */
+  HMG_K_COUNT = 19
 } hmg_kernel_id;
 
 typedef struct {

@@ -68,7 +68,7 @@ class KernelStat(ctypes.Structure):
 
 KERNELS = ["sweep0", "sweep", "prolong", "resid_restrict", "apply", "dot", "update_xr", "update_p", "layout",
            "resid_sq", "assembly", "theta_grad", "ortho", "nlo_sweep", "nlo_resid", "nlo_apply",
-           "nlo_sweep0", "coarse_cycle"]
+           "nlo_sweep0", "coarse_cycle", "halo"]
 
 
 class PartInfo(ctypes.Structure):
@@ -121,6 +121,7 @@ _SIGNATURES = {
     "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
     "hmg_convert_fp32_to_fp64": [_P, _P, ctypes.c_int64, _P],
     "hmg_set_coarse_fusion": [_P, _I],
+    "hmg_partition": [_P, _I],
     "hmg_partition_info": [_I, _I, _I, _I, _I, ctypes.POINTER(PartInfo)],
     "hmg_partition_tables": [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P],
     "hmg_profile_start": [_P, ctypes.c_uint, ctypes.c_uint],
@@ -443,6 +444,11 @@ class Hierarchy:
         self._check(self.lib.hmg_to_layout(self._ctx, level, LAYOUT[src], _ptr(v.contiguous()), LAYOUT[dst],
                                            _ptr(out), _stream(stream)))
         return out
+
+    def partition(self, nparts):
+        """Run as nparts parts of the horizontal domain decomposition, emulated
+        on this device (include/hmg.h, hmg_partition); 1 = unpartitioned."""
+        self._check(self.lib.hmg_partition(self._ctx, int(nparts)))
 
     def set_coarse_fusion(self, enable):
         """Run the coarse end of each V-cycle as one cooperative kernel (True,

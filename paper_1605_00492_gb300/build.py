@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["mesh.cpp", "assemble.cu", "cycle.cu", "krylov.cu", "gmres.cu", "mixed.cu", "nlo.cu", "nlo_mixed.cu", "nlo_setup.cpp", "capi.cu", "noalloc.cu", "partition.cpp"]
+SOURCES = ["mesh.cpp", "assemble.cu", "cycle.cu", "krylov.cu", "gmres.cu", "mixed.cu", "nlo.cu", "nlo_mixed.cu", "nlo_setup.cpp", "capi.cu", "noalloc.cu", "partition.cpp", "halo.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -231,11 +231,306 @@ bool fused_from(const hmg_ctx* c, const CycleCfg& cfg, int lev) {
          cfg.nlev - lev <= CC_MAX_LEVELS;
 }
 
+// ------------------------------------------------------------ domain decomposition
+//
+// A context partitioned into K parts (hmg_partition) runs every level-0
+// V-cycle and level-0 FP64 operator application as K parts, as K processes
+// would: each pass once per part on the part's owned columns, and every pass
+// that reads neighbour columns preceded by a halo exchange (pack, move the
+// (sender, receiver) segments, unpack).  The coarsest level is gathered, solved
+// once and scattered back.  On one device the moves are device copies; each
+// part's passes are the same kernels with the same per-cell arithmetic as the
+// unpartitioned cycle.
+
+size_t dt_size(int dt) { return dt == HMG_FP64 ? sizeof(double) : sizeof(float); }
+
+void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, void* out, int out_dt,
+           cudaStream_t s, const SweepDot* dot);
+
+void exchange(hmg_ctx* c, int lev, int dt, const PartPtrs& v, cudaStream_t s) {
+  hmg_ctx::PartSet& ps = c->psets[lev];
+  if (ps.n_send == 0) return;
+  const int nz = c->lv[lev].nz;
+  void* sb = dt == HMG_FP64 ? ps.send64 : ps.send32;
+  void* rb = dt == HMG_FP64 ? ps.recv64 : ps.recv32;
+  const size_t es = dt_size(dt) * (size_t)nz;
+  LAUNCH(c, HMG_K_HALO, lev, s, launch_halo_pack(ps.n_send, nz, ps.pack_part, ps.pack_col, v, sb, dt, s));
+  for (size_t i = 0; i < ps.copy_n.size(); ++i)
+    cuda_ok(cudaMemcpyAsync(static_cast<char*>(rb) + ps.copy_dst[i] * es,
+                            static_cast<const char*>(sb) + ps.copy_src[i] * es, ps.copy_n[i] * es,
+                            cudaMemcpyDeviceToDevice, s),
+            "halo move");
+  LAUNCH(c, HMG_K_HALO, lev, s, launch_halo_unpack(ps.n_recv, nz, ps.unpack_part, ps.unpack_col, v, rb, dt, s));
+}
+
+// The cycle of cycle() on partitioned level lev; b, out: each part's owned
+// tiles of the right-hand side and of the result.
+void pcycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const PartPtrs& b, int b_dt, const PartPtrs& out,
+            int out_dt, cudaStream_t s) {
+  hmg_ctx::PartSet& ps = c->psets[lev];
+  const int K = c->nparts;
+  const int dt = level_dt(c, cfg, lev);
+  const bool coarsest = lev == cfg.nlev - 1;
+  const int npre = coarsest ? cfg.n_coarse : cfg.nu_pre;
+  PartPtrs A{}, B{}, bl{};
+  for (int p = 0; p < K; ++p) {
+    Level& P = ps.part[p];
+    A.p[p] = work(P, dt, 0);
+    B.p[p] = work(P, dt, 1);
+    float* bcopy = (dt == HMG_FP32 && b_dt == HMG_FP64) ? P.b32 : nullptr;
+    bl.p[p] = bcopy ? (void*)bcopy : b.p[p];
+    const bool direct = coarsest && npre == 1 && out_dt == dt && !bcopy;
+    LAUNCH(c, HMG_K_SWEEP0, lev, s,
+           launch_sweep0(P, dt, b.p[p], b_dt, direct ? out.p[p] : A.p[p], bcopy, cfg.omega, s));
+  }
+  if (coarsest && npre == 1) {
+    if (out_dt != dt || dt == HMG_FP32) throw Fail{HMG_ERR_INVALID_ARG, "unsupported coarsest-level configuration"};
+    return;
+  }
+  PartPtrs cur = A, nxt = B;
+  for (int i = 1; i < npre; ++i) {
+    const bool last = coarsest && i == npre - 1;
+    exchange(c, lev, dt, cur, s);
+    for (int p = 0; p < K; ++p)
+      LAUNCH(c, HMG_K_SWEEP, lev, s,
+             launch_sweep(ps.part[p], dt, bl.p[p], cur.p[p], last ? out.p[p] : nxt.p[p], last ? out_dt : dt,
+                          nullptr, dt, cfg.omega, nullptr, s));
+    if (last) return;
+    std::swap(cur, nxt);
+  }
+  if (coarsest) throw Fail{HMG_ERR_INVALID_ARG, "unsupported coarsest-level configuration"};
+  // residual, restricted into the parts of the next level, or into the
+  // landing arrays of the gathered coarsest level
+  const int cdt = level_dt(c, cfg, lev + 1);
+  const bool land = lev + 1 >= (int)c->psets.size();
+  PartPtrs bc{}, ec{};
+  for (int p = 0; p < K; ++p) {
+    if (land) {
+      bc.p[p] = c->land_b[p];
+      ec.p[p] = c->land_x[p];
+    } else {
+      Level& Q = c->psets[lev + 1].part[p];
+      bc.p[p] = work(Q, cdt, 2);
+      ec.p[p] = cdt == HMG_FP64 ? (void*)Q.ux64 : (void*)Q.ux32;
+    }
+  }
+  exchange(c, lev, dt, cur, s);
+  for (int p = 0; p < K; ++p)
+    LAUNCH(c, HMG_K_RESID_RESTRICT, lev, s,
+           launch_resid_restrict(ps.part[p], dt, bl.p[p], cur.p[p], bc.p[p], cdt, s));
+  if (land) {
+    if (cdt != HMG_FP64) throw Fail{HMG_ERR_INVALID_ARG, "the gathered coarsest level must be FP64"};
+    Level& C = c->lv[lev + 1];
+    for (int p = 0; p < K; ++p)
+      LAUNCH(c, HMG_K_HALO, lev + 1, s,
+             launch_copy_cols(ps.part[p].nc / 4, C.nz, c->land_b[p], 0, C.b64, ps.begin[p] / 4, HMG_FP64, s));
+    cycle(c, cfg, lev + 1, C.b64, HMG_FP64, C.ux64, HMG_FP64, s, nullptr);
+    for (int p = 0; p < K; ++p)
+      LAUNCH(c, HMG_K_HALO, lev + 1, s,
+             launch_copy_cols(ps.part[p].nc / 4, C.nz, C.ux64, ps.begin[p] / 4, c->land_x[p], 0, HMG_FP64, s));
+  } else {
+    pcycle(c, cfg, lev + 1, bc, cdt, ec, cdt, s);
+  }
+  // post-smoothing: the prolonged correction is added by its own pass (the
+  // sweeps then read it, with the neighbours' values, after an exchange)
+  for (int p = 0; p < K; ++p)
+    LAUNCH(c, HMG_K_PROLONG, lev, s, launch_prolong(ps.part[p], dt, cur.p[p], ec.p[p], cdt, s));
+  for (int i = 0; i < cfg.nu_post; ++i) {
+    const bool last = i == cfg.nu_post - 1;
+    exchange(c, lev, dt, cur, s);
+    for (int p = 0; p < K; ++p)
+      LAUNCH(c, HMG_K_SWEEP, lev, s,
+             launch_sweep(ps.part[p], dt, bl.p[p], cur.p[p], last ? out.p[p] : nxt.p[p], last ? out_dt : dt,
+                          nullptr, cdt, cfg.omega, nullptr, s));
+    std::swap(cur, nxt);
+  }
+}
+
+// Free the device side of a partition; the graphs hold its pointers, so they go too.
+void drop_partition(hmg_ctx* c) {
+  for (auto& ps : c->psets) {
+    for (Level& P : ps.part)
+      for (void* v : {(void*)P.nbr, (void*)P.ua64, (void*)P.ub64, (void*)P.b64, (void*)P.ux64, (void*)P.ua32,
+                      (void*)P.ub32, (void*)P.b32, (void*)P.ux32})
+        dfree(c, v);
+    for (void* v : {(void*)ps.pack_part, (void*)ps.pack_col, (void*)ps.unpack_part, (void*)ps.unpack_col,
+                    ps.send64, ps.recv64, ps.send32, ps.recv32})
+      dfree(c, v);
+  }
+  for (double* v : c->land_b) dfree(c, v);
+  for (double* v : c->land_x) dfree(c, v);
+  c->psets.clear();
+  c->land_b.clear();
+  c->land_x.clear();
+  c->nparts = 1;
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    destroy_graph_prof(g.prof);
+  }
+  c->graphs.clear();
+}
+
+template <typename T>
+T* upload(hmg_ctx* c, const std::vector<T>& h) {
+  T* d = dalloc<T>(c, h.size());
+  if (!h.empty()) cuda_ok(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+  return d;
+}
+
+// The device side of a K-part partition: each part's view of every
+// partitioned level (its owned columns of the level's coefficient arrays,
+// which are whole tiles, a local neighbour table and local work vectors with
+// room for the ghost columns), the exchange tables, and the landing arrays
+// of the gathered coarsest level.
+void build_partition_dev(hmg_ctx* c, int K) {
+  std::vector<std::vector<int32_t>> nbr;
+  std::vector<int> ncols;
+  for (const Level& L : c->lv) {
+    nbr.push_back(L.nbr_host);
+    ncols.push_back(L.nc);
+  }
+  const PartitionPlan plan = build_partition(nbr, ncols, K);
+  c->nparts = K;
+  c->psets.resize(plan.nlevels);
+  for (int l = 0; l < plan.nlevels; ++l) {
+    const Level& G = c->lv[l];
+    hmg_ctx::PartSet& ps = c->psets[l];
+    ps.part.resize(K);
+    ps.begin.resize(K);
+    std::vector<int32_t> pk_part, pk_col, up_part, up_col;
+    std::vector<int64_t> send_off(K + 1, 0), recv_off(K + 1, 0);
+    for (int p = 0; p < K; ++p) {
+      const PartLevel& pl = plan.lv[l][p];
+      send_off[p + 1] = send_off[p] + (int64_t)pl.send_col.size();
+      recv_off[p + 1] = recv_off[p] + (int64_t)pl.ghost_col.size();
+    }
+    for (int p = 0; p < K; ++p) {
+      const PartLevel& pl = plan.lv[l][p];
+      ps.begin[p] = pl.begin;
+      Level& P = ps.part[p];
+      P.refinement = G.refinement;
+      P.nc = pl.n_own;
+      P.ncp = pl.n_own_pad;
+      P.nz = G.nz;
+      P.twist = G.twist;
+      P.N = (int64_t)P.nc * P.nz;
+      P.Np = (int64_t)P.ncp * P.nz;
+      const int64_t cell0 = (int64_t)pl.begin * G.nz;   // whole tiles: the part's tiles start here
+      P.gh = G.gh + pl.begin;
+      P.gh32 = G.gh32 + pl.begin;
+      P.mt = G.mt + pl.begin;
+      P.mt32 = G.mt32 + pl.begin;
+      P.d = G.d + cell0;
+      P.e = G.e + cell0;
+      P.lo = G.lo + cell0;
+      P.w = G.w + cell0;
+      P.d32 = G.d32 + cell0;
+      P.e32 = G.e32 + cell0;
+      P.lo32 = G.lo32 + cell0;
+      P.w32 = G.w32 + cell0;
+      std::vector<int4> nb(P.ncp);
+      for (int col = 0; col < P.ncp; ++col)
+        nb[col] = col < P.nc ? make_int4(pl.local_nbr[3 * col], pl.local_nbr[3 * col + 1], pl.local_nbr[3 * col + 2], 0)
+                             : make_int4(col, col, col, 0);
+      P.nbr = upload(c, nb);
+      const int64_t ghost_tiles = ((int64_t)pl.ghost_col.size() + TW - 1) / TW;
+      const int64_t with_ghosts = (P.ncp + ghost_tiles * TW) * P.nz;
+      P.ua64 = dalloc<double>(c, with_ghosts);
+      P.ub64 = dalloc<double>(c, with_ghosts);
+      P.ua32 = dalloc<float>(c, with_ghosts);
+      P.ub32 = dalloc<float>(c, with_ghosts);
+      P.b64 = dalloc<double>(c, P.Np);
+      P.ux64 = dalloc<double>(c, P.Np);
+      P.b32 = dalloc<float>(c, P.Np);
+      P.ux32 = dalloc<float>(c, P.Np);
+      for (size_t i = 0; i < pl.send_col.size(); ++i) {
+        pk_part.push_back(p);
+        pk_col.push_back(pl.send_col[i] - pl.begin);
+      }
+      for (size_t i = 0; i < pl.ghost_col.size(); ++i) {
+        up_part.push_back(p);
+        up_col.push_back(pl.n_own_pad + (int32_t)i);
+      }
+      // the (p -> q) segments: p's send list is grouped by receiver, q's
+      // ghosts by owner, both in q's ghost order
+      for (int q = 0; q < K; ++q) {
+        if (q == p) continue;
+        const auto s0 = std::find(pl.send_to.begin(), pl.send_to.end(), q);
+        const int64_t n = std::count(pl.send_to.begin(), pl.send_to.end(), q);
+        if (n == 0) continue;
+        const PartLevel& ql = plan.lv[l][q];
+        const auto g0 = std::find(ql.ghost_owner.begin(), ql.ghost_owner.end(), p);
+        ps.copy_src.push_back(send_off[p] + (s0 - pl.send_to.begin()));
+        ps.copy_dst.push_back(recv_off[q] + (g0 - ql.ghost_owner.begin()));
+        ps.copy_n.push_back(n);
+      }
+    }
+    ps.n_send = (int)pk_part.size();
+    ps.n_recv = (int)up_part.size();
+    require(ps.n_send == ps.n_recv, "partition: send and receive lists differ in length");
+    ps.pack_part = upload(c, pk_part);
+    ps.pack_col = upload(c, pk_col);
+    ps.unpack_part = upload(c, up_part);
+    ps.unpack_col = upload(c, up_col);
+    const size_t entries = (size_t)std::max(ps.n_send, 1) * G.nz;
+    ps.send64 = dalloc<double>(c, entries);
+    ps.recv64 = dalloc<double>(c, entries);
+    ps.send32 = dalloc<float>(c, entries);
+    ps.recv32 = dalloc<float>(c, entries);
+  }
+  if (plan.nlevels < (int)c->lv.size()) {   // landing arrays of the gathered coarsest level
+    const Level& C = c->lv[plan.nlevels];
+    for (int p = 0; p < K; ++p) {
+      const int ncl = c->psets.back().part[p].nc / 4;
+      const size_t cells = (size_t)((ncl + TW - 1) / TW) * TW * C.nz;
+      c->land_b.push_back(dalloc<double>(c, cells));
+      c->land_x.push_back(dalloc<double>(c, cells));
+    }
+  }
+}
+
+// Each part's owned tiles of a level-0 tiled vector.
+PartPtrs part_slices(const hmg_ctx* c, const void* v, int dt) {
+  PartPtrs r{};
+  const hmg_ctx::PartSet& ps = c->psets[0];
+  for (int p = 0; p < c->nparts; ++p)
+    r.p[p] = static_cast<char*>(const_cast<void*>(v)) + (size_t)ps.begin[p] * c->lv[0].nz * dt_size(dt);
+  return r;
+}
+
+// y = H^ x on level 0 (FP64, tiled), partitioned when the context is; with
+// red, x.y is reduced as well (over all parts: the allreduce of the dot).
+void apply_fine(hmg_ctx* c, const double* x, double* y, const Reduce* red, cudaStream_t s) {
+  Level& L = c->lv[0];
+  if (c->nparts <= 1) {
+    LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, x, y, red, s));
+    return;
+  }
+  hmg_ctx::PartSet& ps = c->psets[0];
+  PartPtrs xl{};
+  const PartPtrs xs = part_slices(c, x, HMG_FP64), ys = part_slices(c, y, HMG_FP64);
+  for (int p = 0; p < c->nparts; ++p) {
+    Level& P = ps.part[p];
+    xl.p[p] = P.ua64;
+    cuda_ok(cudaMemcpyAsync(P.ua64, xs.p[p], (size_t)P.Np * sizeof(double), cudaMemcpyDeviceToDevice, s),
+            "part operand");
+  }
+  exchange(c, 0, HMG_FP64, xl, s);
+  for (int p = 0; p < c->nparts; ++p)
+    LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(ps.part[p], HMG_FP64, xl.p[p], ys.p[p], nullptr, s));
+  if (red) LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, x, y, nullptr, nullptr, *red, s));
+}
+
 // out <- V_lev b (zero initial guess).  b has type b_dt, out has type out_dt;
 // out must not be one of the level's work buffers ua / ub.  `dot` (optional)
 // is fused into the last sweep of this level.
 void cycle(hmg_ctx* c, const CycleCfg& cfg, int lev, const void* b, int b_dt, void* out, int out_dt,
            cudaStream_t s, const SweepDot* dot = nullptr) {
+  if (lev == 0 && c->nparts > 1) {
+    if (dot) throw Fail{HMG_ERR_INVALID_ARG, "a fused dot product is not available on a partitioned cycle"};
+    pcycle(c, cfg, 0, part_slices(c, b, b_dt), b_dt, part_slices(c, out, out_dt), out_dt, s);
+    return;
+  }
   Level& L = c->lv[lev];
   const int nlev = cfg.nlev;
   const int dt = level_dt(c, cfg, lev);
@@ -334,8 +629,7 @@ SweepDot beta_dot(const hmg_ctx* c, bool flexible) {
 // (holding their outputs for the dots costs the registers that let the
 // column recurrence run ahead of its loads).
 bool fused_beta(const hmg_ctx* c, const CycleCfg& cfg) {
-  (void)c;
-  return !cfg.mixed && (cfg.nlev > 1 || cfg.n_coarse > 1);
+  return !cfg.mixed && (cfg.nlev > 1 || cfg.n_coarse > 1) && c->nparts <= 1;
 }
 
 void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t s, bool read_back = true) {
@@ -351,7 +645,7 @@ void iteration_body(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cudaStream_t
   }
   LAUNCH(c, HMG_K_UPDATE_P, 0, s, launch_update_p(L, c->kp, c->kz, c->red.sc, s));
   Reduce ra = red_with(c, EPI_ALPHA);
-  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s));
+  apply_fine(c, c->kp, c->kq, &ra, s);
   LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
   if (read_back)
     cuda_ok(cudaMemcpyAsync(c->host_sc, c->red.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s),
@@ -546,7 +840,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     }
     cuda_ok(cudaMemcpyAsync(c->kp, c->kz, bytes, cudaMemcpyDeviceToDevice, s), "copy");
     Reduce ra = red_with(c, EPI_ALPHA);
-    LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kp, c->kq, &ra, s));
+    apply_fine(c, c->kp, c->kq, &ra, s);
     LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
     const double stop2 = p.rtol * p.rtol * bb;
     if (!c->prof_on && p.max_iter <= CG_LOOP_HIST) {
@@ -589,7 +883,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     }
   }
   // true residual ||b - H^ x|| / ||b||
-  LAUNCH(c, HMG_K_APPLY, 0, s, launch_apply(L, HMG_FP64, c->kx, c->kq, nullptr, s));
+  apply_fine(c, c->kx, c->kq, nullptr, s);
   LAUNCH(c, HMG_K_RESID_SQ, 0, s, launch_resid_sq(L, c->kb, c->kq, red_with(c, EPI_STORE0, S_TRUE), s));
   cuda_ok(cudaEventRecord(c->ev1, s), "event");
   read_scalars(c, s);
@@ -828,8 +1122,8 @@ hmg_status solve_gmres(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
   sys.b = c->kb;
   sys.x = c->kx;
   sys.tmp = c->kq;
-  sys.apply = [c, &L](const double* x, double* y, cudaStream_t st) {
-    LAUNCH(c, HMG_K_APPLY, 0, st, launch_apply(L, HMG_FP64, x, y, nullptr, st));
+  sys.apply = [c](const double* x, double* y, cudaStream_t st) {
+    apply_fine(c, x, y, nullptr, st);
   };
   sys.precond = [c, cfg](const double* r, double* z, cudaStream_t st) {
     cycle(c, cfg, 0, r, HMG_FP64, z, HMG_FP64, st);
@@ -1417,12 +1711,16 @@ hmg_status hmg_apply(hmg_ctx* ctx, int level, int dtype, int layout, const void*
     need_assembled(ctx);
     cudaStream_t s = as_stream(stream);
     Level& L = ctx->lv[level];
+    // level 0 in FP64 runs partitioned on a partitioned context
+    const bool part = level == 0 && dtype == HMG_FP64 && ctx->nparts > 1;
     if (layout == HMG_LAYOUT_TILED) {
-      LAUNCH(ctx, HMG_K_APPLY, level, s, launch_apply(L, dtype, x, y, nullptr, s));
+      if (part) apply_fine(ctx, (const double*)x, (double*)y, nullptr, s);
+      else LAUNCH(ctx, HMG_K_APPLY, level, s, launch_apply(L, dtype, x, y, nullptr, s));
       return;
     }
     LAUNCH(ctx, HMG_K_LAYOUT, level, s, launch_to_tiled(L, dtype, x, ctx->kcol, s));
-    LAUNCH(ctx, HMG_K_APPLY, level, s, launch_apply(L, dtype, ctx->kcol, ctx->kcol2, nullptr, s));
+    if (part) apply_fine(ctx, ctx->kcol, ctx->kcol2, nullptr, s);
+    else LAUNCH(ctx, HMG_K_APPLY, level, s, launch_apply(L, dtype, ctx->kcol, ctx->kcol2, nullptr, s));
     LAUNCH(ctx, HMG_K_LAYOUT, level, s, launch_to_column(L, dtype, ctx->kcol2, y, s));
   });
 }
@@ -1764,7 +2062,7 @@ const char* hmg_kernel_name(int kernel) {
   static const char* names[HMG_K_COUNT] = {"sweep0", "sweep",     "prolong",  "resid_restrict", "apply",
                                            "dot",    "update_xr", "update_p", "layout",         "resid_sq",
                                            "assembly", "theta_grad", "ortho",    "nlo_sweep",      "nlo_resid",
-                                           "nlo_apply", "nlo_sweep0", "coarse_cycle"};
+                                           "nlo_apply", "nlo_sweep0", "coarse_cycle", "halo"};
   return (kernel >= 0 && kernel < HMG_K_COUNT) ? names[kernel] : "?";
 }
 
@@ -1806,6 +2104,23 @@ hmg_status hmg_partition_tables(int refinement, int nlevels, int nparts, int par
     put(pl.local_nbr, local_nbr);
     put(pl.send_col, send_col);
     put(pl.send_to, send_to);
+  });
+}
+
+hmg_status hmg_partition(hmg_ctx* ctx, int nparts) {
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    require(nparts >= 1 && nparts <= MAX_PARTS, "nparts must be in [1, 16]");
+    cuda_ok(cudaDeviceSynchronize(), "partition");
+    drop_partition(ctx);
+    if (nparts > 1) {
+      try {
+        build_partition_dev(ctx, nparts);
+      } catch (...) {
+        drop_partition(ctx);
+        throw;
+      }
+    }
   });
 }
 

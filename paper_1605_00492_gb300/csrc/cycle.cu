@@ -1025,7 +1025,7 @@ __device__ __forceinline__ void cc_resid(const CoarseArgs& a, int k, const T* b,
 }
 
 template <bool MIXED, int NW>
-__global__ void __launch_bounds__(NW * 32) k_coarse_cycle(const __grid_constant__ CoarseArgs a) {
+__global__ void __launch_bounds__(NW * 32, 2) k_coarse_cycle(const __grid_constant__ CoarseArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   cg::grid_group grid = cg::this_grid();
   const int last = a.nlev - 1;
@@ -1096,7 +1096,8 @@ __global__ void __launch_bounds__(NW * 32) k_coarse_cycle(const __grid_constant_
 
 template <bool MIXED>
 cudaError_t coarse_cycle_launch(const CoarseArgs& a, size_t smem, cudaStream_t s) {
-  constexpr int NW = NW_SWEEP_SMALL;
+  // 8 warps and two CTAs per SM: a level of up to 304 tiles takes one tile per CTA
+  constexpr int NW = 8;
   auto kern = k_coarse_cycle<MIXED, NW>;
   static SmemOptIn opt_in;
   cudaError_t e = allow_smem(kern, smem, opt_in);

@@ -26,7 +26,7 @@
 namespace hmg {
 
 constexpr int TW = 32;                 // columns per tile
-constexpr int SMALL_LEVEL_TILES = 152;  // levels with at most this many tiles are latency bound
+constexpr int SMALL_LEVEL_TILES = 160;  // levels with at most this many tiles are latency bound
 constexpr int FUSED_PROLONG_MAX_TILES = 160;  // FP64 levels up to this size fuse prolongation into the sweep
 // The coarse end of the V-cycle, from the first level of at most
 // CC_MAX_TILES tiles (below the finest) down, runs as one cooperative kernel.
@@ -284,6 +284,20 @@ struct SweepDot {
 void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo, int uo_dt, const void* ec,
                   int ec_dt, double omega, const SweepDot* dot, cudaStream_t s);
 void launch_prolong(const Level& L, int dt, void* u, const void* ec, int ec_dt, cudaStream_t s);
+// Halo exchange and column copies of the domain decomposition (halo.cu).
+constexpr int MAX_PARTS = 16;
+struct PartPtrs {
+  void* p[MAX_PARTS];
+};
+// buf[e][l] = v.p[part[e]] at (col[e], l), e < n (tiled layout of the part)
+void launch_halo_pack(int n, int nz, const int32_t* part, const int32_t* col, const PartPtrs& v, void* buf, int dt,
+                      cudaStream_t s);
+// v.p[part[e]] at (col[e], l) = buf[e][l]
+void launch_halo_unpack(int n, int nz, const int32_t* part, const int32_t* col, const PartPtrs& v,
+                        const void* buf, int dt, cudaStream_t s);
+// dst column dst0 + c = src column src0 + c, c < ncols, every layer
+void launch_copy_cols(int ncols, int nz, const void* src, int src0, void* dst, int dst0, int dt, cudaStream_t s);
+
 // The V-cycle from level ls (b_in: its right-hand side, out: its result,
 // both of its type) down to level nlev - 1 and back, as one cooperative
 // kernel (cycle.cu, k_coarse_cycle).  Returns the launch's error.
@@ -446,6 +460,26 @@ struct hmg_ctx {
   hmg::GsWork gm{};
   double* gm_y = nullptr;
   double* gm_host = nullptr;      // page-locked copy of gm_small
+  // K-part horizontal domain decomposition emulated on this device
+  // (hmg_partition): per partitioned level, each part's level view and local
+  // vectors, and the halo exchange tables; per part, the landing arrays of
+  // the coarsest level's gather and scatter.
+  struct PartSet {
+    std::vector<hmg::Level> part;              // [part]: owned columns, local neighbours, local work vectors
+    std::vector<int32_t> begin;                // [part] first owned column (global)
+    int n_send = 0, n_recv = 0;
+    int32_t *pack_part = nullptr, *pack_col = nullptr, *unpack_part = nullptr, *unpack_col = nullptr;
+    std::vector<int64_t> copy_src, copy_dst, copy_n;   // segment moves between parts, in entries
+    void* send64 = nullptr;                    // n_send x nz entries (FP64 and FP32 buffers)
+    void* recv64 = nullptr;
+    void* send32 = nullptr;
+    void* recv32 = nullptr;
+  };
+  int nparts = 1;
+  std::vector<PartSet> psets;                  // [partitioned level]
+  std::vector<double*> land_b, land_x;         // [part] coarsest-level landing arrays (FP64)
+  std::vector<double*> part_x0;                // [part] level-0 local copy of an operand (owned + ghosts)
+
   // device-side CG loop: its state (device, through the context's allocator)
   // and a page-locked copy read once after the loop
   hmg::CgLoop* cg_loop = nullptr;
