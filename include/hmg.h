@@ -471,11 +471,13 @@ typedef struct {
 /* Whether V-cycles run their coarse end (Algorithm 1 from the first level
  * below the finest with at most 160 tiles of 32 columns, down to the
  * coarsest and back) as one cooperative kernel with a grid-wide barrier
- * between its sweep and residual passes (enable != 0, the default), or as
- * one kernel per pass.  Both run the same arithmetic in the same order and
- * give identical results; the fused form saves the launch and memory
- * latency of the small levels.  Applies to later calls on this context.
- * Errors: INVALID_ARG (ctx NULL). */
+ * between its sweep and residual passes (enable != 0), or as one kernel per
+ * pass (0, the default).  Both run the same arithmetic in the same order and
+ * give identical results.  The fused form removes the launches of the small
+ * levels, but on GB300 its passes take as long as the separate kernels and
+ * solves that use it measured 4 % (FP64) to 10 % (mixed) slower, so it is
+ * off unless asked for.  Applies to later calls on this context.  Errors: INVALID_ARG (ctx
+ * NULL). */
 hmg_status hmg_set_coarse_fusion(hmg_ctx* ctx, int enable);
 
 /* Tracing (the per-level kernel breakdown of Sec. 5.4): from this call on,

@@ -451,8 +451,8 @@ class Hierarchy:
         self._check(self.lib.hmg_partition(self._ctx, int(nparts)))
 
     def set_coarse_fusion(self, enable):
-        """Run the coarse end of each V-cycle as one cooperative kernel (True,
-        the default) or as one kernel per pass (False); same results."""
+        """Run the coarse end of each V-cycle as one cooperative kernel (True)
+        or as one kernel per pass (False, the default); same results."""
         self._check(self.lib.hmg_set_coarse_fusion(self._ctx, 1 if enable else 0))
 
     def profile_start(self, kernels=None, levels=None):

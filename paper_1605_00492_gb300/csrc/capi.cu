@@ -197,7 +197,7 @@ struct CycleCfg {
   int nu_pre = 2, nu_post = 2, n_coarse = 2;
   int nlev = 1;          // levels used: 0 .. nlev - 1 (nlev = 1: single-level line relaxation)
   bool mixed = false;
-  bool fuse = true;      // coarse end of the cycle as one cooperative kernel
+  bool fuse = false;     // coarse end of the cycle as one cooperative kernel
   double omega = 0.8;
 };
 

@@ -417,7 +417,7 @@ struct hmg_ctx {
   hmg::Phys ph{};
   bool assembled = false;
   bool has_theta = false;
-  bool fuse_coarse = true;        // hmg_set_coarse_fusion
+  bool fuse_coarse = false;       // hmg_set_coarse_fusion (off: measured slower inside solves)
   std::vector<hmg::Level> lv;
   // Krylov vectors on the finest level (tiled) and a column-layout staging buffer
   double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr, *kb = nullptr;

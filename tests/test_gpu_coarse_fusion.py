@@ -3,7 +3,7 @@ level below the finest with at most 160 tiles down to the coarsest and back,
 Algorithm 1) against the same cycle run as one kernel per pass
 (hmg_set_coarse_fusion).  Both evaluate the same sweeps and residuals in the
 same order, so V-cycles and solves agree exactly; the oracle comparisons of
-the other GPU tests run with the fused form, which is the default."""
+the other GPU tests run with the separate kernels, the default."""
 import numpy as np
 import pytest
 
@@ -66,6 +66,7 @@ def test_fused_nlo_vcycle_is_identical():
 def test_fused_kernel_is_traced_as_one_launch():
     h = hmg.Hierarchy(4, 16, 4)
     h.assemble()
+    h.set_coarse_fusion(True)
     b = torch.tensor(gi.rhs(h.ncells), dtype=torch.float64, device="cuda:0")
     h.profile_start()
     h.vcycle(b)
