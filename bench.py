@@ -651,6 +651,9 @@ def run_gpu(args):
     traced_ms, _ = timed_steps(lambda: h.solve(b, out=x, **kw64), args.steps, stream)
     dom_stats = h.profile_stop()
 
+    # ---- the FP64 pipe's throughput on this device (the roof of the FP64 kernels)
+    fp64_probe = h.measure_fp64_rate()
+
     # ---- mixed form, same protocol (no tracing)
     for _ in range(3):
         h.solve(b, out=x, **kwmx)
@@ -716,6 +719,8 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                 "peak_source": "derived FP64 FMA rate (152 SM x 4 x 32 lanes / 64 cycles x 2 x 2.07 GHz)",
+                "peak_probe_TFLOP_s": round(fp64_probe, 4),
+                "frac_of_probe": round(tflops / fp64_probe, 4) if fp64_probe > 0 else None,
                 "hbm_achieved_GB_s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",

@@ -468,6 +468,14 @@ typedef struct {
   double total_ms;  /* sum of CUDA-event durations of those launches */
 } hmg_kernel_stat;
 
+/* Measures the FP64 FMA throughput of the context's device (the bound of the
+ * FP64 cycle's kernels, Sec. 5.4's performance model on this hardware): a
+ * kernel of 8 independent FMA chains per thread on 8 CTAs of 256 threads per
+ * SM, timed with CUDA events on `stream` after a warm-up launch.  Writes
+ * TFLOP/s (2 flops per FMA) to *tflops; synchronises the stream.
+ * Errors: INVALID_ARG, CUDA. */
+hmg_status hmg_measure_fp64_rate(hmg_ctx* ctx, double* tflops, void* stream);
+
 /* Whether V-cycles run their coarse end (Algorithm 1 from the first level
  * below the finest with at most 160 tiles of 32 columns, down to the
  * coarsest and back) as one cooperative kernel with a grid-wide barrier

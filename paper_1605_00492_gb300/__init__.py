@@ -121,6 +121,7 @@ _SIGNATURES = {
     "hmg_convert_fp64_to_fp32": [_P, _P, ctypes.c_int64, _P],
     "hmg_convert_fp32_to_fp64": [_P, _P, ctypes.c_int64, _P],
     "hmg_set_coarse_fusion": [_P, _I],
+    "hmg_measure_fp64_rate": [_P, ctypes.POINTER(ctypes.c_double), _P],
     "hmg_partition": [_P, _I],
     "hmg_partition_info": [_I, _I, _I, _I, _I, ctypes.POINTER(PartInfo)],
     "hmg_partition_tables": [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P],
@@ -444,6 +445,12 @@ class Hierarchy:
         self._check(self.lib.hmg_to_layout(self._ctx, level, LAYOUT[src], _ptr(v.contiguous()), LAYOUT[dst],
                                            _ptr(out), _stream(stream)))
         return out
+
+    def measure_fp64_rate(self, stream=None):
+        """FP64 FMA throughput of this device in TFLOP/s (include/hmg.h)."""
+        v = ctypes.c_double()
+        self._check(self.lib.hmg_measure_fp64_rate(self._ctx, ctypes.byref(v), _stream(stream)))
+        return v.value
 
     def partition(self, nparts):
         """Run as nparts parts of the horizontal domain decomposition, emulated

@@ -2124,6 +2124,15 @@ hmg_status hmg_partition(hmg_ctx* ctx, int nparts) {
   });
 }
 
+hmg_status hmg_measure_fp64_rate(hmg_ctx* ctx, double* tflops, void* stream) {
+  if (!ctx || !tflops) return HMG_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    *tflops = measure_fp64_fma_rate(ctx->red.partials, as_stream(stream));
+    launched("k_fp64_fma_probe");
+    ctx->launches += 2;
+  });
+}
+
 hmg_status hmg_set_coarse_fusion(hmg_ctx* ctx, int enable) {
   if (!ctx) return HMG_ERR_INVALID_ARG;
   ctx->fuse_coarse = enable != 0;

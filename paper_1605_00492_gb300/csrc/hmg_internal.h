@@ -328,6 +328,9 @@ struct CgLoop {
   double hist[CG_LOOP_HIST];
 };
 void launch_cg_loop_init(CgLoop* loop, double rtol2, int max_iter, cudaStream_t s);
+// FP64 FMA throughput of this device in TFLOP/s (krylov.cu, k_fp64_fma_probe);
+// synchronises the stream.
+double measure_fp64_fma_rate(double* sink, cudaStream_t s);
 void launch_cg_control(CgLoop* loop, const double* sc, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_update_xr(const Level& L, double* x, double* r, const double* p, const double* q,
                       const Reduce& red, cudaStream_t s);

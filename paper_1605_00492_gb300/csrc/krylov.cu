@@ -263,4 +263,44 @@ void launch_cg_loop_init(CgLoop* loop, double rtol2, int max_iter, cudaStream_t 
   k_cg_loop_init<<<1, 32, 0, s>>>(loop, rtol2, max_iter);
 }
 
+// Throughput probe of the FP64 FMA pipe (the bound of the FP64 cycle): every
+// thread advances 8 independent FMA chains, so each warp always has an FP64
+// instruction ready.  The result is stored only if it is not finite, which it
+// never is for these inputs; the test keeps the chains live.
+__global__ void k_fp64_fma_probe(int iters, double* __restrict__ sink) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * k + 1e-9 * threadIdx.x;
+  const double m = 0.9999999, c = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += a[k];
+  if (!isfinite(t)) sink[0] = t;
+}
+
+double measure_fp64_fma_rate(double* sink, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = 8 * (sms > 0 ? sms : 152), threads = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fp64_fma_probe<<<blocks, threads, 0, s>>>(64, sink);   // warm-up
+  cudaEventRecord(e0, s);
+  k_fp64_fma_probe<<<blocks, threads, 0, s>>>(iters, sink);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  return ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+}
+
 }  // namespace hmg
