@@ -143,9 +143,18 @@ typedef void (*hmg_release_fn)(void* ptr, void* user);
 hmg_status hmg_build_hierarchy_with_allocator(const hmg_mesh_params* params, hmg_alloc_fn alloc,
                                               hmg_release_fn release, void* user, hmg_ctx** out);
 
-/* Release every resource of a context (NULL is accepted). */
+/* Release every resource of a context: its device memory (through the
+ * caller's release callback when it was built with one), page-locked host
+ * buffers, events, its capture stream and captured graphs.  Synchronises
+ * the current device first (all its work, not only the context's).  NULL is
+ * accepted (no-op).  Always returns HMG_OK. */
 hmg_status hmg_destroy(hmg_ctx* ctx);
 
+/* Sizes of one level of the hierarchy (level 0 = finest, refinement
+ * `refinement` of the build; level k has refinement - k) into *out:
+ * columns 20 * 4^refinement, their count padded to a multiple of 32 (the
+ * TILED layout), layers, and cells in both layouts.  Host only, no device
+ * work.  Errors: INVALID_ARG (ctx or out NULL, level outside [0, nlevels)). */
 hmg_status hmg_get_level_info(const hmg_ctx* ctx, int level, hmg_level_info* out);
 
 /* Copy one level's mesh to caller-owned host buffers (any may be NULL):
