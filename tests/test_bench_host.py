@@ -88,3 +88,13 @@ def test_useful_bandwidth_from_a_breakdown():
     assert ub["sweep@0"]["us_per_launch"] == pytest.approx(100.0)
     assert ub["apply@0"]["TFLOP_s"] == pytest.approx(11 * cells[0] / 0.08e-3 / 1e12, rel=1e-3)
     assert 0 < ub["sweep0@1"]["frac_hbm"] < 1
+
+
+def test_cpu_baseline_runs_one_oracle_copy_per_core():
+    """The CPU baseline runs single-threaded copies of the oracle side by
+    side and sums their solves/s; each copy times the same bounded sample."""
+    d = bench.cpu_baseline_subprocess("r3x16", 1, copies=2)
+    assert d["kind"] == "oracle" and d["cores"] == 2 and d["unit"] == bench.UNIT
+    lo, hi = d["seconds_per_solve_min_max"]
+    assert 0 < lo <= hi
+    assert 2 / hi - 1e-9 <= d["value"] <= 2 / lo + 1e-9
