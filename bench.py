@@ -740,6 +740,28 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(n * 8), "ms_per_step": round(ms_e2e, 4),
                "ms_per_step_stats": step_stats(per_e2e)}
 
+    # ---- the horizontal domain decomposition of Sec. 5 emulated on this GPU:
+    # K parts with real halo exchanges (pack, segment moves, unpack) before
+    # every pass that reads neighbour columns, the coarsest level gathered
+    part = None
+    if not args.no_extra:
+        part = {"what": "FP64 PCG solves of the same problem on K parts of one GPU (hmg_partition); the halo "
+                        "exchange's share from one traced solve"}
+        for K in (2, 4):
+            h.partition(K)
+            for _ in range(2):
+                _, ik = h.solve(b, out=x, **kw64)
+            reps = max(5, min(args.steps, 20))
+            totk, perk = timed_steps(lambda: h.solve(b, out=x, **kw64), reps, stream)
+            h.profile_start()
+            h.solve(b, out=x, **kw64)
+            brk = h.profile_stop()
+            halo_ms = sum(t for (k, _), (_, t) in brk.items() if k == "halo")
+            all_ms = sum(t for _, (_, t) in brk.items())
+            part[f"K{K}"] = {"solves_per_s": round(reps / (totk / 1e3), 3), "ms_per_solve": step_stats(perk),
+                             "iterations": ik["iterations"], "halo_share_of_traced_time": round(halo_ms / all_ms, 4)}
+        h.partition(1)
+
     # ---- the other workloads: r3x16 latency, r5x64a adjoint, r7x128 both forms
     small = None if args.no_extra else small_config_section(args, dev, stream)
     adjoint = None if args.no_extra else adjoint_section(args, dev, stream)
@@ -788,6 +810,7 @@ def run_gpu(args):
                   "iterations": infomx["iterations"], "true_rel_residual": infomx["true_rel_residual"],
                   "rel_l2_vs_fp64_solution": err_mx,
                   "krylov": "flexible CG", "dtype": "f32 cycle / f64 Krylov + coarsest"},
+        "partition_emulated": part,
         "r3x16": small,
         "r5x64a_adjoint": adjoint,
         "r7x128": large,
