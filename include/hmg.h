@@ -440,9 +440,11 @@ hmg_status hmg_sync(hmg_ctx* ctx, void* stream);
  * address (with that device current); make that first call before any
  * stream capture.  All calls share the array: calls whose work overlaps on
  * the GPU (other streams, other threads) race and must be ordered by the
- * caller.  Each call overwrites every staging entry it reads.  Errors:
- * INVALID_ARG (bad level or pointers, or ncells_padded of the level above
- * HMG_NOALLOC_MAX_CELLS), STATE (not assembled), CUDA. */
+ * caller.  Each call overwrites every staging entry it reads.  Its three
+ * launches (layout, operator, layout) are traced and counted like
+ * hmg_apply's.  Errors: INVALID_ARG (bad level or pointers, or
+ * ncells_padded of the level above HMG_NOALLOC_MAX_CELLS), STATE (not
+ * assembled), OOM (host allocation of an error message), CUDA. */
 hmg_status hmg_apply_noalloc(hmg_ctx* ctx, int level, const double* x, double* y, void* stream);
 
 /* Kernel classes reported by the tracing calls below. */
