@@ -721,7 +721,26 @@ void harvest_body(hmg_ctx* c, const hmg_ctx::BodyGraph* g) {
   }
 }
 
-// The CG iterations after the first as one CUDA graph: a stopping-test
+// The first CG iteration: z = V r with r.z, p = z, q = H^ p with alpha,
+// x += alpha p, r -= alpha q with r.r.
+void first_iteration(hmg_ctx* c, const CycleCfg& cfg, cudaStream_t s) {
+  Level& L = c->lv[0];
+  if (fused_beta(c, cfg)) {
+    SweepDot d;
+    d.a = c->kr;
+    d.red = red_with(c, EPI_INIT_RZ);
+    cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s, &d);
+  } else {
+    cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
+    LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, c->kr, c->kz, nullptr, nullptr, red_with(c, EPI_INIT_RZ), s));
+  }
+  cuda_ok(cudaMemcpyAsync(c->kp, c->kz, (size_t)L.Np * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  Reduce ra = red_with(c, EPI_ALPHA);
+  apply_fine(c, c->kp, c->kq, &ra, s);
+  LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
+}
+
+// The CG iterations as one CUDA graph: the first iteration, a stopping-test
 // kernel (k_cg_control), then a while node whose body is one iteration
 // followed by the same test, so the whole loop runs without the host.  The
 // test sets the node's condition; it ends the loop at max_iter at the
@@ -737,29 +756,47 @@ hmg_ctx::BodyGraph* run_loop(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cud
     cudaStream_t cs = c->capture_stream;
     cudaGraph_t graph = nullptr;
     cuda_ok(cudaGraphCreate(&graph, 0), "graph create");
-    int body_kernels = 0;
+    int body_kernels = 0, first_kernels = 0;
     try {
       cudaGraphConditionalHandle hnd;
       cuda_ok(cudaGraphConditionalHandleCreate(&hnd, graph, 0, cudaGraphCondAssignDefault), "conditional handle");
+      // the first iteration and the first test, then the while node after them
+      cudaGraph_t body = nullptr;
+      const int64_t before0 = c->launches;
       cuda_ok(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
               "begin capture");
-      launch_cg_control(c->cg_loop, c->red.sc, hnd, cs);
-      cudaError_t le = cudaGetLastError();
+      c->capturing = true;
+      try {
+        first_iteration(c, cfg, cs);
+        launch_cg_control(c->cg_loop, c->red.sc, hnd, cs);
+        launched("k_cg_control");
+        c->launches += 1;
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cuda_ok(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps), "capture info");
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hnd;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode = nullptr;
+        cuda_ok(cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &np), "while node");
+        cuda_ok(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies),
+                "capture dependencies");
+        body = np.conditional.phGraph_out[0];
+      } catch (...) {
+        c->capturing = false;
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(cs, &dummy);
+        c->launches = before0;
+        throw;
+      }
+      c->capturing = false;
+      first_kernels = (int)(c->launches - before0);
+      c->launches = before0;
       cudaGraph_t same = nullptr;
       cuda_ok(cudaStreamEndCapture(cs, &same), "end capture");
-      cuda_ok(le, "k_cg_control");
-      cudaGraphNode_t first = nullptr;
-      size_t nn = 1;
-      cuda_ok(cudaGraphGetNodes(graph, &first, &nn), "graph nodes");
-      if (nn != 1) throw Fail{HMG_ERR_CUDA, "loop graph: unexpected node count"};
-      cudaGraphNodeParams np{};
-      np.type = cudaGraphNodeTypeConditional;
-      np.conditional.handle = hnd;
-      np.conditional.type = cudaGraphCondTypeWhile;
-      np.conditional.size = 1;
-      cudaGraphNode_t wnode = nullptr;
-      cuda_ok(cudaGraphAddNode(&wnode, graph, &first, nullptr, 1, &np), "while node");
-      cudaGraph_t body = np.conditional.phGraph_out[0];
       const int64_t before = c->launches;
       cuda_ok(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
               "begin capture");
@@ -789,6 +826,7 @@ hmg_ctx::BodyGraph* run_loop(hmg_ctx* c, const CycleCfg& cfg, bool flexible, cud
     bg.key = key;
     bg.trace = 0;
     bg.kernels = body_kernels;
+    bg.first_kernels = first_kernels;
     cudaError_t e = cudaGraphInstantiate(&bg.exec, graph, 0);
     cudaGraphDestroy(graph);
     cuda_ok(e, "graph instantiate");
@@ -828,20 +866,6 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     inf.converged = 1;
     st = HMG_OK;
   } else {
-    // first iteration: p = z = V r
-    if (fused_beta(c, cfg)) {
-      SweepDot d;
-      d.a = c->kr;
-      d.red = red_with(c, EPI_INIT_RZ);
-      cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s, &d);
-    } else {
-      cycle(c, cfg, 0, c->kr, HMG_FP64, c->kz, HMG_FP64, s);
-      LAUNCH(c, HMG_K_DOT, 0, s, launch_dot(L, c->kr, c->kz, nullptr, nullptr, red_with(c, EPI_INIT_RZ), s));
-    }
-    cuda_ok(cudaMemcpyAsync(c->kp, c->kz, bytes, cudaMemcpyDeviceToDevice, s), "copy");
-    Reduce ra = red_with(c, EPI_ALPHA);
-    apply_fine(c, c->kp, c->kq, &ra, s);
-    LAUNCH(c, HMG_K_UPDATE_XR, 0, s, launch_update_xr(L, c->kx, c->kr, c->kp, c->kq, red_with(c, EPI_RR), s));
     const double stop2 = p.rtol * p.rtol * bb;
     if (!c->prof_on && p.max_iter <= CG_LOOP_HIST) {
       // device-side loop: one graph launch; its state is read with the
@@ -855,6 +879,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
       loop_graph = run_loop(c, cfg, flexible, s);
       cuda_ok(cudaMemcpyAsync(c->cg_loop_host, c->cg_loop, sizeof(CgLoop), cudaMemcpyDeviceToHost, s), "loop read");
     } else {
+      first_iteration(c, cfg, s);
       read_scalars(c, s);
       for (int k = 1;; ++k) {
         inf.iterations = k;
@@ -891,7 +916,7 @@ hmg_status solve_tiled(hmg_ctx* c, const hmg_solve_params& p, hmg_solve_info* in
     const CgLoop& lh = *c->cg_loop_host;
     const int k = lh.k;
     if (k < 1 || k > p.max_iter) throw Fail{HMG_ERR_CUDA, "device loop returned an invalid iteration count"};
-    c->launches += 1 + (int64_t)(k - 1) * loop_graph->kernels;
+    c->launches += loop_graph->first_kernels + (int64_t)(k - 1) * loop_graph->kernels;
     inf.iterations = k;
     c->history.assign(lh.hist, lh.hist + k);
     inf.rel_residual = c->history.back();

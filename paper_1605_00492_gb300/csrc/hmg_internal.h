@@ -448,6 +448,7 @@ struct hmg_ctx {
     unsigned long long trace = 0;   // tracing masks the graph was captured with (0: none)
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;
+    int first_kernels = 0;          // device-side CG loop: launches before the while node
     std::vector<hmg::GraphProf> prof;
   };
   std::vector<BodyGraph> graphs;
