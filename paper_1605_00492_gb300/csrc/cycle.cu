@@ -186,7 +186,12 @@ __device__ __forceinline__ void tsweep_tile(const LD<T>& L, const int tile, cons
           r = fma(g.y, a1[i], r);
           r = fma(g.z, a2[i], r);
         }
-        if (bcopy && valid) bcopy[base + (int64_t)l * TW] = (float)bl[i];
+        // the FP32 copy of an FP64 right-hand side exists only on FP32
+        // levels; for FP64 levels the conversion is compiled out, so it can
+        // never be executed speculatively on the FP64 pipe
+        if constexpr (std::is_same<T, float>::value && std::is_same<TB, double>::value) {
+          if (bcopy && valid) bcopy[base + (int64_t)l * TW] = (float)bl[i];
+        }
         R[l * TW + lane] = r;
         LOs[l * TW + lane] = lo[i];
       }
