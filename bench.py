@@ -473,14 +473,15 @@ def velocity_pressure_section(h, args, world, dev, stream, ev0, ev1):
         for _ in range(2):
             h.mixed_solve(bu, bp, **kwvp)
         reps = max(5, min(args.steps, 20))
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(reps):
-            _, _, infovp = h.mixed_solve(bu, bp, **kwvp)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / reps
+        res = {}
+
+        def step():
+            res["info"] = h.mixed_solve(bu, bp, **kwvp)[2]
+        tot, per = timed_steps(step, reps, stream)
+        ms = max_over_ranks(tot, world, dev) / reps
+        infovp = res["info"]
         vp[form] = {"solves_per_s": round(world / (ms / 1e3), 3), "ms_per_solve": round(ms, 4),
+                    "ms_per_solve_stats": step_stats(per),
                     "iterations": infovp["iterations"], "true_rel_residual": infovp["true_rel_residual"]}
     return vp
 
