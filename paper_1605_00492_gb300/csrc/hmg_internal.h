@@ -482,7 +482,6 @@ struct hmg_ctx {
   int nparts = 1;
   std::vector<PartSet> psets;                  // [partitioned level]
   std::vector<double*> land_b, land_x;         // [part] coarsest-level landing arrays (FP64)
-  std::vector<double*> part_x0;                // [part] level-0 local copy of an operand (owned + ghosts)
 
   // device-side CG loop: its state (device, through the context's allocator)
   // and a page-locked copy read once after the loop
