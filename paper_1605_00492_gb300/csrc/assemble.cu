@@ -123,10 +123,13 @@ __global__ void k_bands(BandArgs a, int64_t Np, double* __restrict__ d, double* 
 // with the same 3 operations per cell as a Thomas solve.  Stored per cell:
 //   lo[l] = lambda_l (l <= m, lo[0] = 0), mu_l (m < l < nz - 1), 0 at l = nz - 1
 //   w[l]  = omega / D_l
-// and per column mt = mu_m (0 when m = nz - 1).
+// and per column mt = mu_m (0 when m = nz - 1).  Computed in FP64; TF = float
+// rounds the FP64 factors once as they are stored (the FP32 copies, which may
+// twist at another row).
+template <typename TF>
 __global__ void k_ldl(int nc, int nz, int m, double omega, const double* __restrict__ d,
-                      const double* __restrict__ e, double* __restrict__ lo, double* __restrict__ w,
-                      double* __restrict__ mt) {
+                      const double* __restrict__ e, TF* __restrict__ lo, TF* __restrict__ w,
+                      TF* __restrict__ mt) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int64_t s = tile_base(c, nz);
@@ -259,16 +262,14 @@ void launch_bands(const Level& L, const Phys& ph, cudaStream_t s) {
 }
 
 void launch_ldl(const Level& L, double omega, cudaStream_t s) {
-  k_ldl<<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist, omega, L.d, L.e, L.lo, L.w, L.mt);
+  k_ldl<double><<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist, omega, L.d, L.e, L.lo, L.w, L.mt);
+  k_ldl<float><<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist32, omega, L.d, L.e, L.lo32, L.w32, L.mt32);
 }
 
 void launch_to_fp32(const Level& L, cudaStream_t s) {
   unsigned g = blocks_for(L.Np, 256);
   k_to_fp32<<<g, 256, 0, s>>>(L.Np, L.d, L.d32);
   k_to_fp32<<<g, 256, 0, s>>>(L.Np, L.e, L.e32);
-  k_to_fp32<<<g, 256, 0, s>>>(L.Np, L.lo, L.lo32);
-  k_to_fp32<<<g, 256, 0, s>>>(L.Np, L.w, L.w32);
-  k_to_fp32<<<blocks_for(L.ncp, 128), 128, 0, s>>>(L.ncp, L.mt, L.mt32);
   k_gh_to_fp32<<<blocks_for(L.ncp, 128), 128, 0, s>>>(L.ncp, L.gh, L.gh32);
 }
 

@@ -413,6 +413,7 @@ void build_partition_dev(hmg_ctx* c, int K) {
       P.ncp = pl.n_own_pad;
       P.nz = G.nz;
       P.twist = G.twist;
+      P.twist32 = G.twist32;
       P.N = (int64_t)P.nc * P.nz;
       P.Np = (int64_t)P.ncp * P.nz;
       const int64_t cell0 = (int64_t)pl.begin * G.nz;   // whole tiles: the part's tiles start here
@@ -1581,9 +1582,11 @@ static hmg_status build_hierarchy(const hmg_mesh_params* p, hmg_alloc_fn alloc, 
       L.nz = p->nlayers;
       L.N = (int64_t)L.nc * L.nz;
       L.Np = (int64_t)L.ncp * L.nz;
-      // twisted two-chain column solves on the small (latency-bound) levels,
-      // the same tile threshold as the 16-warp sweep CTAs of cycle.cu
-      L.twist = (L.ncp / TW <= SMALL_LEVEL_TILES) ? L.nz / 2 : L.nz - 1;
+      // FP64: half columns on two warps everywhere; FP32: twisted two-chain
+      // column solves on the small (latency-bound) levels, the same tile
+      // threshold as the staged FP32 sweep of cycle.cu
+      L.twist = L.nz / 2;
+      L.twist32 = (L.ncp / TW <= SMALL_LEVEL_TILES) ? L.nz / 2 : L.nz - 1;
       L.centroid_host = H.centroid;
       L.nbr_host = H.nbr;
       L.verts_host = H.verts;
@@ -1718,8 +1721,8 @@ hmg_status hmg_assemble_helmholtz(hmg_ctx* ctx, const hmg_op_params* p, const do
       LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_couplings(L, ph.wc2 * ph.dz, s));
       LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_bands(L, ph, s));
       L.theta = th;
-      LAUNCH(ctx, HMG_K_ASSEMBLY, lev, s, launch_ldl(L, ph.omega, s));
-      LAUNCHN(ctx, HMG_K_ASSEMBLY, lev, s, 6, launch_to_fp32(L, s));
+      LAUNCHN(ctx, HMG_K_ASSEMBLY, lev, s, 2, launch_ldl(L, ph.omega, s));
+      LAUNCHN(ctx, HMG_K_ASSEMBLY, lev, s, 3, launch_to_fp32(L, s));
     }
     cuda_ok(cudaStreamSynchronize(s), "assemble");
     ctx->assembled = true;

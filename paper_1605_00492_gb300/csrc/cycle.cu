@@ -51,7 +51,7 @@ template <> LD<double> view<double>(const Level& L) {
   return LD<double>{L.nc, L.nz, L.Np, L.nbr, L.gh, L.d, L.e, L.lo, L.w, L.mt, L.twist};
 }
 template <> LD<float> view<float>(const Level& L) {
-  return LD<float>{L.nc, L.nz, L.Np, L.nbr, L.gh32, L.d32, L.e32, L.lo32, L.w32, L.mt32, L.twist};
+  return LD<float>{L.nc, L.nz, L.Np, L.nbr, L.gh32, L.d32, L.e32, L.lo32, L.w32, L.mt32, L.twist32};
 }
 
 __device__ __forceinline__ int64_t tile_base(int c, int nz) {
@@ -372,6 +372,232 @@ k_tsweep(LD<T> L, const TB* __restrict__ b, const T* __restrict__ u, TO* __restr
          const TE* __restrict__ ec, float* __restrict__ bcopy, T om1, const double* __restrict__ da,
          const double* __restrict__ dc, Reduce red) {
   tsweep_tile<T, TB, TO, MODE, TE, NW, DOT, TW2>(L, blockIdx.x, b, u, uo, ec, bcopy, om1, da, dc, red);
+}
+
+// ---------------------------------------------------------------- FP64 half-column sweep
+//
+// FP64 levels.  The FP64 pipe issues one warp instruction per 64 cycles per
+// SM sub-partition, and a dependent FMA is ready exactly when the next may
+// issue, so one warp whose operands are in registers keeps a sub-partition's
+// pipe busy on its own.  Here each tile is relaxed by a pair of warps, one
+// per half of the twisted factorisation N D N^T of H^_z (twist row m): the
+// top warp eliminates rows 0..m-1 downwards, the bottom warp rows nz-1..m+1
+// upwards, lane = column.  A row's right-hand side R = b + sum_k g_k u~[nbr_k]
+// is formed as the row is eliminated, from loads issued RB rows at a time,
+// and the unscaled y_l is parked in the row's output cell (each lane reads
+// back only what it wrote; uo is never u).  The pair swaps y_m-1, y_m+1 and
+// R_m through shared memory at one 64-thread named barrier, both warps
+// complete the twist row, x_m = (omega / D_m)(R_m - lambda_m y_m-1 - mu_m y_m+1),
+// and each substitutes outwards through its half, scaling by omega / D_l and
+// relaxing, u' = (1 - omega) u~ + x, as it goes.  The recurrences never touch
+// shared memory, and no CTA-wide barrier holds a warp.  Two tiles per CTA.
+//
+// u~ = u, or u + P e_c with the coarse correction e_c (MODE_PRO); MODE_ZERO
+// relaxes from u = 0.  DOT as in tsweep_tile.
+template <int MODE, int DOT, int RB, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_hsweep(LD<double> L, int ntiles, const double* __restrict__ b, const double* __restrict__ u,
+         double* __restrict__ uo, const double* __restrict__ ec, double om1, const double* __restrict__ da,
+         const double* __restrict__ dc, Reduce red) {
+  constexpr int TPB = 2;
+  __shared__ double xch[TPB][3][TW];   // y_m-1, y_m+1, R_m of each tile
+  __shared__ double scratch[DOT ? 2 * TPB * 64 : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pair = warp >> 1, half = warp & 1;
+  const int tile = blockIdx.x * TPB + pair;
+  const int nz = L.nz, m = L.twist;
+  const int c = tile * TW + lane;
+  const bool valid = tile < ntiles && c < L.nc;
+  const int64_t base = (int64_t)tile * TW * nz + lane;
+  int64_t s0 = 0, s1 = 0, s2 = 0, q = 0, q0 = 0, q1 = 0, q2 = 0;
+  double4_32a g{};
+  if (MODE != MODE_ZERO && valid) {
+    const int4 nb = L.nbr[c];
+    g = L.gh[c];
+    s0 = tile_base(nb.x, nz);
+    s1 = tile_base(nb.y, nz);
+    s2 = tile_base(nb.z, nz);
+    if (MODE == MODE_PRO) {
+      q = tile_base(c >> 2, nz);
+      q0 = tile_base(nb.x >> 2, nz);
+      q1 = tile_base(nb.y >> 2, nz);
+      q2 = tile_base(nb.z >> 2, nz);
+    }
+  }
+  // rows of this half before the twist row, walked away from the ends
+  const int cnt = half ? nz - 1 - m : m;
+  const int64_t st = half ? -(int64_t)TW : (int64_t)TW;
+  const int64_t o0 = half ? (int64_t)(nz - 1) * TW : 0;
+  // Both passes are software pipelined: the loads of the next RB rows are
+  // issued before the arithmetic of the current ones, and a row's store is
+  // issued one batch later, when its value is long ready (the FP64 result of
+  // a recurrence would otherwise hold up the warp's in-order issue).
+  double y = 0.0;
+  if (valid) {
+    double cb[RB], cl[RB], c0[RB], c1[RB], c2[RB], ys[RB];
+    auto fload = [&](int k, double (&xb)[RB], double (&xl)[RB], double (&x0)[RB], double (&x1)[RB],
+                     double (&x2)[RB]) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        xb[i] = xl[i] = x0[i] = x1[i] = x2[i] = 0.0;
+        if (k + i < cnt) {
+          const int64_t o = o0 + (k + i) * st;
+          xb[i] = b[base + o];
+          xl[i] = L.lo[base + o];
+          if (MODE != MODE_ZERO) {
+            x0[i] = u[s0 + o];
+            x1[i] = u[s1 + o];
+            x2[i] = u[s2 + o];
+            if (MODE == MODE_PRO) {
+              x0[i] += ec[q0 + o];
+              x1[i] += ec[q1 + o];
+              x2[i] += ec[q2 + o];
+            }
+          }
+        }
+      }
+    };
+    fload(0, cb, cl, c0, c1, c2);
+#pragma unroll
+    for (int i = 0; i < RB; ++i) ys[i] = 0.0;
+    int k = 0;
+    for (; k < cnt; k += RB) {
+      double nb[RB], nl[RB], n0[RB], n1[RB], n2[RB];
+      fload(k + RB, nb, nl, n0, n1, n2);
+      if (k > 0) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) uo[base + o0 + (k - RB + i) * st] = ys[i];
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        double r = cb[i];
+        if (MODE != MODE_ZERO) {
+          r = fma(g.x, c0[i], r);
+          r = fma(g.y, c1[i], r);
+          r = fma(g.z, c2[i], r);
+        }
+        if (k + i < cnt) y = fma(-cl[i], y, r);
+        ys[i] = y;
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        cb[i] = nb[i];
+        cl[i] = nl[i];
+        c0[i] = n0[i];
+        c1[i] = n1[i];
+        c2[i] = n2[i];
+      }
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        if (k - RB + i < cnt) uo[base + o0 + (k - RB + i) * st] = ys[i];
+    }
+  }
+  // the twist row: R_m from the top warp, y_m-1 / y_m+1 from each side
+  const int64_t om = (int64_t)m * TW;
+  if (half == 0) {
+    double r = 0.0;
+    if (valid) {
+      r = b[base + om];
+      if (MODE != MODE_ZERO) {
+        double a0 = u[s0 + om], a1 = u[s1 + om], a2 = u[s2 + om];
+        if (MODE == MODE_PRO) {
+          a0 += ec[q0 + om];
+          a1 += ec[q1 + om];
+          a2 += ec[q2 + om];
+        }
+        r = fma(g.x, a0, r);
+        r = fma(g.y, a1, r);
+        r = fma(g.z, a2, r);
+      }
+    }
+    xch[pair][2][lane] = r;
+    xch[pair][0][lane] = y;
+  } else {
+    xch[pair][1][lane] = y;
+  }
+  if (pair == 0) asm volatile("barrier.sync 1, 64;" ::: "memory");
+  else asm volatile("barrier.sync 2, 64;" ::: "memory");
+  double acc0 = 0.0, acc1 = 0.0;
+  if (valid) {
+    const double lam = L.lo[base + om], wm = L.w[base + om], mu = L.mt[c];
+    const double ym = fma(-mu, xch[pair][1][lane], fma(-lam, xch[pair][0][lane], xch[pair][2][lane]));
+    double x = wm * ym;
+    if (half == 0) {   // the top warp writes the twist row
+      double ut = 0.0;
+      if (MODE != MODE_ZERO) {
+        ut = u[base + om];
+        if (MODE == MODE_PRO) ut += ec[q + om];
+      }
+      const double out = (MODE == MODE_ZERO) ? x : fma(om1, ut, x);
+      uo[base + om] = out;
+      if (DOT) acc0 = fma(da[base + om], out, acc0);
+      if (DOT == 2) acc1 = fma(out, dc[base + om], acc1);
+    }
+    // outwards from the twist row: rows m-1..0 (top), m+1..nz-1 (bottom);
+    // the first multiplier is lambda_m (top) or mu_m (bottom)
+    double mprev = half ? mu : lam;
+    const int64_t bst = -st, b0 = om + bst;
+    double cy[RB], cw[RB], cl[RB], cu[RB], ca[RB], cc[RB], outs[RB];
+    auto bload = [&](int k, double (&xy)[RB], double (&xw)[RB], double (&xl)[RB], double (&xu)[RB],
+                     double (&xa)[RB], double (&xc)[RB]) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        xy[i] = xw[i] = xl[i] = xu[i] = xa[i] = xc[i] = 0.0;
+        if (k + i < cnt) {
+          const int64_t o = b0 + (k + i) * bst;
+          xy[i] = uo[base + o];
+          xw[i] = L.w[base + o];
+          xl[i] = L.lo[base + o];
+          if (MODE != MODE_ZERO) {
+            xu[i] = u[base + o];
+            if (MODE == MODE_PRO) xu[i] += ec[q + o];
+          }
+          if (DOT) xa[i] = da[base + o];
+          if (DOT == 2) xc[i] = dc[base + o];
+        }
+      }
+    };
+    bload(0, cy, cw, cl, cu, ca, cc);
+#pragma unroll
+    for (int i = 0; i < RB; ++i) outs[i] = 0.0;
+    int k = 0;
+    for (; k < cnt; k += RB) {
+      double ny[RB], nw[RB], nl[RB], nu[RB], na[RB], nc[RB];
+      bload(k + RB, ny, nw, nl, nu, na, nc);
+      if (k > 0) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) uo[base + b0 + (k - RB + i) * bst] = outs[i];
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        if (k + i < cnt) {
+          x = fma(-mprev, x, cw[i] * cy[i]);
+          mprev = cl[i];
+          const double out = (MODE == MODE_ZERO) ? x : fma(om1, cu[i], x);
+          outs[i] = out;
+          if (DOT) acc0 = fma(ca[i], out, acc0);
+          if (DOT == 2) acc1 = fma(out, cc[i], acc1);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        cy[i] = ny[i];
+        cw[i] = nw[i];
+        cl[i] = nl[i];
+        cu[i] = nu[i];
+        ca[i] = na[i];
+        cc[i] = nc[i];
+      }
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        if (k - RB + i < cnt) uo[base + b0 + (k - RB + i) * bst] = outs[i];
+    }
+  }
+  if (DOT) grid_reduce<(DOT == 2 ? 2 : 1)>(acc0, acc1, red, scratch);
 }
 
 // ---------------------------------------------------------------- FP32 staged sweep
@@ -950,6 +1176,28 @@ bool rsweep(const Level& L, const void* b, const void* u, void* uo, const void* 
   }
 }
 
+// FP64 levels: the half-column sweep, two tiles per CTA
+constexpr int HSWEEP_RB = 1;     // rows per batch of loads
+constexpr int HSWEEP_MINB = 9;   // resident CTAs per SM: the finest level in one wave
+
+template <int MODE, int DOT>
+void hsweep_k(const Level& L, const void* b, const void* u, void* uo, const void* ec, double omega,
+              const SweepDot* dot, cudaStream_t s) {
+  const int nt = ntiles_of(L);
+  const Reduce red = dot ? dot->red : Reduce{};
+  k_hsweep<MODE, DOT, HSWEEP_RB, HSWEEP_MINB><<<(nt + 1) / 2, 128, 0, s>>>(
+      view<double>(L), nt, (const double*)b, (const double*)u, (double*)uo, (const double*)ec, 1.0 - omega,
+      dot ? dot->a : nullptr, dot ? dot->c : nullptr, red);
+}
+
+template <int MODE>
+void hsweep(const Level& L, const void* b, const void* u, void* uo, const void* ec, double omega, cudaStream_t s,
+            const SweepDot* dot = nullptr) {
+  if (!dot) hsweep_k<MODE, 0>(L, b, u, uo, ec, omega, dot, s);
+  else if (!dot->c) hsweep_k<MODE, 1>(L, b, u, uo, ec, omega, dot, s);
+  else hsweep_k<MODE, 2>(L, b, u, uo, ec, omega, dot, s);
+}
+
 template <typename T, typename TB, typename TO, int MODE, typename TE>
 void tsweep(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
             cudaStream_t s, const SweepDot* dot = nullptr) {
@@ -957,6 +1205,32 @@ void tsweep(const Level& L, const void* b, const void* u, void* uo, const void* 
     tsweep_dot<T, TB, TO, MODE, TE, NW_SWEEP_BIG>(L, b, u, uo, ec, bcopy, omega, dot, s);
   else
     tsweep_dot<T, TB, TO, MODE, TE, NW_SWEEP_SMALL>(L, b, u, uo, ec, bcopy, omega, dot, s);
+}
+
+// FP64 levels (factors twisted at nz / 2): the half-column sweep on large
+// levels; on small ones, where a lone warp per sub-partition would wait on
+// its loads, the 16-warp tile sweep with its twisted two-chain solve.
+constexpr int HSWEEP_MIN_TILES = SMALL_LEVEL_TILES;
+
+template <int MODE, int NW>
+void tsweep_twisted(const Level& L, const void* b, const void* u, void* uo, const void* ec, double omega,
+                    const SweepDot* dot, cudaStream_t s) {
+  if (!dot) tsweep_k<double, double, double, MODE, double, NW, 0, true>(L, b, u, uo, ec, nullptr, omega, dot, s);
+  else if (!dot->c)
+    tsweep_k<double, double, double, MODE, double, NW, 1, true>(L, b, u, uo, ec, nullptr, omega, dot, s);
+  else tsweep_k<double, double, double, MODE, double, NW, 2, true>(L, b, u, uo, ec, nullptr, omega, dot, s);
+}
+
+template <int MODE>
+void fp64_sweep(const Level& L, const void* b, const void* u, void* uo, const void* ec, double omega,
+                cudaStream_t s, const SweepDot* dot = nullptr) {
+  const int nt = ntiles_of(L);
+  if (nt > HSWEEP_MIN_TILES)
+    hsweep<MODE>(L, b, u, uo, ec, omega, s, dot);
+  else if (nt > SMALL_LEVEL_TILES)
+    tsweep_twisted<MODE, NW_SWEEP_BIG>(L, b, u, uo, ec, omega, dot, s);
+  else
+    tsweep_twisted<MODE, NW_SWEEP_SMALL>(L, b, u, uo, ec, omega, dot, s);
 }
 
 // ---------------------------------------------------------------- fused coarse levels
@@ -1132,7 +1406,7 @@ cudaError_t coarse_cycle_launch(const CoarseArgs& a, size_t smem, cudaStream_t s
 void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, float* bcopy, double omega,
                    cudaStream_t s) {
   if (dt == HMG_FP64)
-    tsweep<double, double, double, MODE_ZERO, double>(L, b, nullptr, u, nullptr, nullptr, omega, s);
+    fp64_sweep<MODE_ZERO>(L, b, nullptr, u, nullptr, omega, s);
   else if (ntiles_of(L) > STAGED_MAX_TILES && b_dt == HMG_FP64 &&
            rsweep<double, float, MODE_ZERO, float>(L, b, nullptr, u, nullptr, bcopy, omega, s))
     return;
@@ -1150,8 +1424,8 @@ void launch_sweep0(const Level& L, int dt, const void* b, int b_dt, void* u, flo
 void launch_sweep(const Level& L, int dt, const void* b, const void* u, void* uo, int uo_dt, const void* ec,
                   int ec_dt, double omega, const SweepDot* dot, cudaStream_t s) {
   if (dt == HMG_FP64) {
-    if (ec) tsweep<double, double, double, MODE_PRO, double>(L, b, u, uo, ec, nullptr, omega, s, dot);
-    else tsweep<double, double, double, MODE_PLAIN, double>(L, b, u, uo, nullptr, nullptr, omega, s, dot);
+    if (ec) fp64_sweep<MODE_PRO>(L, b, u, uo, ec, omega, s, dot);
+    else fp64_sweep<MODE_PLAIN>(L, b, u, uo, nullptr, omega, s, dot);
     return;
   }
   const bool out64 = uo_dt == HMG_FP64;

@@ -11,7 +11,9 @@
 //   lo, w double[Np]     twisted factorisation N D N^T of H^_z (twist at
 //                        layer `twist`): multipliers and omega / D_l
 //   mt    double[ncp]    the second multiplier of the twist row
-//   *32                  FP32 copies for the mixed-precision cycle
+//   *32                  FP32 copies for the mixed-precision cycle (lo32,
+//                        w32, mt32: the factorisation twisted at `twist32`,
+//                        computed in FP64 and rounded once)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,10 +72,13 @@ PartitionPlan build_partition_for_mesh(int refinement, int nlevels, int nparts);
 
 struct Level {
   int refinement = 0, nc = 0, ncp = 0, nz = 0;
-  // twist row of the column factorisation: nz / 2 on small levels (two
+  // twist rows of the column factorisations.  FP64 factors (lo, w, mt):
+  // nz / 2 on every level (the FP64 sweep relaxes each half column on its own
+  // warp).  FP32 factors (lo32, w32, mt32): nz / 2 on small levels (two
   // half-length recurrences, latency bound), nz - 1 elsewhere (one recurrence:
-  // the plain L D L^T, which measured faster on throughput-bound levels)
+  // the plain L D L^T of the register-column FP32 sweep).
   int twist = 0;
+  int twist32 = 0;
   int64_t N = 0, Np = 0;
   std::vector<double> centroid_host;
   std::vector<int32_t> nbr_host;
