@@ -1051,6 +1051,19 @@ constexpr int NW_SWEEP_BIG = 4;
 // beats the register-batched one; on larger levels it does not.
 constexpr int STAGED_MAX_TILES = 160;
 constexpr int NW_SWEEP_SMALL = 16;
+constexpr int NW_SWEEP_MID = 8;
+
+// SMs of the current device, looked up once.
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n = v > 0 ? v : 152;
+  }
+  return n;
+}
 
 inline int ntiles_of(const Level& L) { return L.ncp / TW; }
 
@@ -1180,14 +1193,23 @@ bool rsweep(const Level& L, const void* b, const void* u, void* uo, const void* 
 constexpr int HSWEEP_RB = 1;     // rows per batch of loads
 constexpr int HSWEEP_MINB = 9;   // resident CTAs per SM: the finest level in one wave
 
+// Levels with fewer than 8 tiles per SM keep fewer pairs per SM; they take
+// four rows per batch of loads (deeper prefetch, 4 CTAs per SM).
+constexpr int HSWEEP_DEEP_TILES_PER_SM = 8;
+
 template <int MODE, int DOT>
 void hsweep_k(const Level& L, const void* b, const void* u, void* uo, const void* ec, double omega,
               const SweepDot* dot, cudaStream_t s) {
   const int nt = ntiles_of(L);
   const Reduce red = dot ? dot->red : Reduce{};
-  k_hsweep<MODE, DOT, HSWEEP_RB, HSWEEP_MINB><<<(nt + 1) / 2, 128, 0, s>>>(
-      view<double>(L), nt, (const double*)b, (const double*)u, (double*)uo, (const double*)ec, 1.0 - omega,
-      dot ? dot->a : nullptr, dot ? dot->c : nullptr, red);
+  if (nt < HSWEEP_DEEP_TILES_PER_SM * num_sms())
+    k_hsweep<MODE, DOT, 4, 4><<<(nt + 1) / 2, 128, 0, s>>>(
+        view<double>(L), nt, (const double*)b, (const double*)u, (double*)uo, (const double*)ec, 1.0 - omega,
+        dot ? dot->a : nullptr, dot ? dot->c : nullptr, red);
+  else
+    k_hsweep<MODE, DOT, HSWEEP_RB, HSWEEP_MINB><<<(nt + 1) / 2, 128, 0, s>>>(
+        view<double>(L), nt, (const double*)b, (const double*)u, (double*)uo, (const double*)ec, 1.0 - omega,
+        dot ? dot->a : nullptr, dot ? dot->c : nullptr, red);
 }
 
 template <int MODE>
@@ -1229,6 +1251,8 @@ void fp64_sweep(const Level& L, const void* b, const void* u, void* uo, const vo
     hsweep<MODE>(L, b, u, uo, ec, omega, s, dot);
   else if (nt > SMALL_LEVEL_TILES)
     tsweep_twisted<MODE, NW_SWEEP_BIG>(L, b, u, uo, ec, omega, dot, s);
+  else if (nt > num_sms())   // one 16-warp CTA per SM: 8-warp CTAs keep the level in one wave
+    tsweep_twisted<MODE, NW_SWEEP_MID>(L, b, u, uo, ec, omega, dot, s);
   else
     tsweep_twisted<MODE, NW_SWEEP_SMALL>(L, b, u, uo, ec, omega, dot, s);
 }
