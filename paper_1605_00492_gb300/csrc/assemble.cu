@@ -125,11 +125,14 @@ __global__ void k_bands(BandArgs a, int64_t Np, double* __restrict__ d, double* 
 //   w[l]  = omega / D_l
 // and per column mt = mu_m (0 when m = nz - 1).  Computed in FP64; TF = float
 // rounds the FP64 factors once as they are stored (the FP32 copies, which may
-// twist at another row).
+// twist at another row).  Optionally (los, mts not null) the multipliers
+// scaled to their own row's pivot, lambda_l D_l-1 / D_l = e_l / D_l and
+// mu_l D_l+1 / D_l = e_l+1 / D_l: with them the elimination runs directly in
+// z = (omega / D) y, z_l = (omega / D_l) R_l - los_l z_l-1 (resp. z_l+1).
 template <typename TF>
 __global__ void k_ldl(int nc, int nz, int m, double omega, const double* __restrict__ d,
                       const double* __restrict__ e, TF* __restrict__ lo, TF* __restrict__ w,
-                      TF* __restrict__ mt) {
+                      TF* __restrict__ mt, TF* __restrict__ los, TF* __restrict__ mts) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int64_t s = tile_base(c, nz);
@@ -139,12 +142,14 @@ __global__ void k_ldl(int nc, int nz, int m, double omega, const double* __restr
     double D = d[at(0)];
     lo[at(0)] = 0.0;
     w[at(0)] = omega / D;
+    if (los) los[at(0)] = 0.0;
     for (int l = 1; l < m; ++l) {
       const double el = e[at(l)];
       const double lam = el / D;
       D = d[at(l)] - lam * el;
       lo[at(l)] = lam;
       w[at(l)] = omega / D;
+      if (los) los[at(l)] = el / D;
     }
     Dtop = D;
   }
@@ -152,12 +157,14 @@ __global__ void k_ldl(int nc, int nz, int m, double omega, const double* __restr
     double D = d[at(nz - 1)];
     lo[at(nz - 1)] = 0.0;
     w[at(nz - 1)] = omega / D;
+    if (los) los[at(nz - 1)] = 0.0;
     for (int l = nz - 2; l > m; --l) {
       const double eu = e[at(l + 1)];
       const double mu = eu / D;
       D = d[at(l)] - mu * eu;
       lo[at(l)] = mu;
       w[at(l)] = omega / D;
+      if (los) los[at(l)] = eu / D;
     }
     Dbot = D;
   }
@@ -176,6 +183,10 @@ __global__ void k_ldl(int nc, int nz, int m, double omega, const double* __restr
   lo[at(m)] = lam_m;
   w[at(m)] = omega / Dm;
   mt[c] = mu_m;
+  if (los) {
+    los[at(m)] = m >= 1 ? e[at(m)] / Dm : 0.0;
+    mts[c] = m <= nz - 2 ? e[at(m + 1)] / Dm : 0.0;
+  }
 }
 
 __global__ void k_to_fp32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -262,8 +273,10 @@ void launch_bands(const Level& L, const Phys& ph, cudaStream_t s) {
 }
 
 void launch_ldl(const Level& L, double omega, cudaStream_t s) {
-  k_ldl<double><<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist, omega, L.d, L.e, L.lo, L.w, L.mt);
-  k_ldl<float><<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist32, omega, L.d, L.e, L.lo32, L.w32, L.mt32);
+  k_ldl<double><<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist, omega, L.d, L.e, L.lo, L.w, L.mt, L.los,
+                                                     L.mts);
+  k_ldl<float><<<blocks_for(L.nc, 64), 64, 0, s>>>(L.nc, L.nz, L.twist32, omega, L.d, L.e, L.lo32, L.w32, L.mt32,
+                                                    nullptr, nullptr);
 }
 
 void launch_to_fp32(const Level& L, cudaStream_t s) {

@@ -420,6 +420,8 @@ void build_partition_dev(hmg_ctx* c, int K) {
       P.gh = G.gh + pl.begin;
       P.gh32 = G.gh32 + pl.begin;
       P.mt = G.mt + pl.begin;
+      P.mts = G.mts + pl.begin;
+      P.los = G.los + cell0;
       P.mt32 = G.mt32 + pl.begin;
       P.d = G.d + cell0;
       P.e = G.e + cell0;
@@ -1614,6 +1616,8 @@ static hmg_status build_hierarchy(const hmg_mesh_params* p, hmg_alloc_fn alloc, 
       L.lo32 = dalloc<float>(c, L.Np);
       L.w32 = dalloc<float>(c, L.Np);
       L.mt = dalloc<double>(c, L.ncp);
+      L.los = dalloc<double>(c, L.Np);
+      L.mts = dalloc<double>(c, L.ncp);
       L.mt32 = dalloc<float>(c, L.ncp);
       L.theta = dalloc<double>(c, L.Np);
       L.b64 = dalloc<double>(c, L.Np);

@@ -44,14 +44,17 @@ struct LD {
   const T* __restrict__ w;
   const T* __restrict__ mt;   // per column: mu of the twist row
   int twist;                  // twist row m of the column factorisation
+  const T* __restrict__ los;  // FP64: multipliers scaled to their row's pivot (e / D)
+  const T* __restrict__ mts;  // FP64: the twist row's mu scaled the same way
 };
 
 template <typename T> LD<T> view(const Level& L);
 template <> LD<double> view<double>(const Level& L) {
-  return LD<double>{L.nc, L.nz, L.Np, L.nbr, L.gh, L.d, L.e, L.lo, L.w, L.mt, L.twist};
+  return LD<double>{L.nc, L.nz, L.Np, L.nbr, L.gh, L.d, L.e, L.lo, L.w, L.mt, L.twist, L.los, L.mts};
 }
 template <> LD<float> view<float>(const Level& L) {
-  return LD<float>{L.nc, L.nz, L.Np, L.nbr, L.gh32, L.d32, L.e32, L.lo32, L.w32, L.mt32, L.twist32};
+  return LD<float>{L.nc, L.nz, L.Np, L.nbr, L.gh32, L.d32, L.e32, L.lo32, L.w32, L.mt32, L.twist32, nullptr,
+                   nullptr};
 }
 
 __device__ __forceinline__ int64_t tile_base(int c, int nz) {
@@ -60,20 +63,26 @@ __device__ __forceinline__ int64_t tile_base(int c, int nz) {
 
 // ---------------------------------------------------------------- sweeps
 //
-// One CTA per tile of 32 columns, NW warps, two shared arrays of nz x 32:
-//   A  (all warps, layer parallel)  R = b + sum_k g_k u[nbr_k]   (u~ with PRO)
-//                                   LO = multipliers of the twisted N D N^T
+// One CTA per tile of 32 columns, NW warps, shared arrays of nz x 32.
+// Twisted solve (twist row m of the level):
+//   A  (all warps, layer parallel)  R = b + sum_k g_k u[nbr_k]   (u~ with PRO),
+//                                   LO = multipliers of N D N^T, and W
 //   B  (two warps: lane = column)   elimination N y = R: rows 0..m-1 top-down
 //                                   on one warp, rows nz-1..m+1 bottom-up on
-//                                   another (m = twist row of the level)
-//   B' (all warps)                  z_l = (omega / D_l) y_l; row m first
-//                                   completes y_m = R_m - lambda_m y_m-1 - mu_m y_m+1
-//   C  (two warps)                  substitution N^T x = z outwards from row m
+//                                   another, each row stored as z_l = (omega / D_l) y_l
+//   C  (the same two warps)         both complete the twist row,
+//                                   x_m = (omega / D_m)(R_m - lambda_m y_m-1 - mu_m y_m+1),
+//                                   then substitute N^T x = z outwards from row m
 //   D  (all warps)                  u' = (1 - omega) u~ + x
-// Only the recurrences are sequential (two chains of about nz / 2 steps on
-// two warps), and they read shared memory, so they never wait for global
-// memory; everything else is spread over the CTA.  MODE_ZERO is the first pre-smoothing step (u = 0):
-// no neighbour sum and no relaxation term.
+// In FP64, W holds the multipliers scaled to their own row's pivot and A
+// scales R by omega / D, so B eliminates directly in z with one FMA per row;
+// in FP32, W = omega / D and B scales each y as it completes.
+// Plain L D L^T (twist row nz - 1, FP32 levels only): one chain warp, and the
+// scaling by omega / D is a layer-parallel phase B' between B and C.
+// Only the recurrences are sequential, and they read shared memory, so they
+// never wait for global memory; everything else is spread over the CTA.
+// MODE_ZERO is the first pre-smoothing step (u = 0): no neighbour sum and no
+// relaxation term.
 enum { MODE_ZERO = 0, MODE_PLAIN = 1, MODE_PRO = 2 };
 
 // count steps of y <- R[l] - LO[l + mshift] y; R[l] = y at l = l0, l0 + step,
@@ -103,6 +112,41 @@ __device__ __forceinline__ T chain(T* R, const T* LO, int lane, int l0, int step
   return y;
 }
 
+// count steps of y <- R[l] - LO[l] y with R[l] = W[l] y stored (the row
+// scaled by omega / D_l as soon as it is eliminated); returns the last y,
+// unscaled.  Shared-memory loads are issued four steps ahead.
+template <typename T>
+__device__ __forceinline__ T chain_scaled(T* R, const T* LO, const T* W, int lane, int l0, int step, int count,
+                                          T y) {
+  int k = 0;
+  for (; k + 4 <= count; k += 4) {
+    const int la = l0 + k * step, lb = la + step, lc = lb + step, ld = lc + step;
+    const T r0 = R[la * TW + lane], r1 = R[lb * TW + lane], r2 = R[lc * TW + lane], r3 = R[ld * TW + lane];
+    const T m0 = LO[la * TW + lane], m1 = LO[lb * TW + lane], m2 = LO[lc * TW + lane], m3 = LO[ld * TW + lane];
+    const T w0 = W[la * TW + lane], w1 = W[lb * TW + lane], w2 = W[lc * TW + lane], w3 = W[ld * TW + lane];
+    const T y0 = fma(-m0, y, r0);
+    const T y1 = fma(-m1, y0, r1);
+    const T y2 = fma(-m2, y1, r2);
+    y = fma(-m3, y2, r3);
+    R[la * TW + lane] = w0 * y0;
+    R[lb * TW + lane] = w1 * y1;
+    R[lc * TW + lane] = w2 * y2;
+    R[ld * TW + lane] = w3 * y;
+  }
+  for (; k < count; ++k) {
+    const int l = l0 + k * step;
+    y = fma(-LO[l * TW + lane], y, R[l * TW + lane]);
+    R[l * TW + lane] = W[l * TW + lane] * y;
+  }
+  return y;
+}
+
+// Spare shared rows after R of the tile sweep: y_m-1, y_m+1 (and, twisted,
+// R_m, mu_m and the scaled mu_m).  The twisted solve also stages a third
+// nz x 32 array: omega / D (FP32) or the scaled multipliers (FP64).
+__host__ __device__ constexpr int tsweep_spare_rows(bool twisted) { return twisted ? 5 : 2; }
+__host__ __device__ constexpr int tsweep_arrays(bool twisted) { return twisted ? 3 : 2; }
+
 // DOT = 1: also reduce sum_cells da * u' (the r.z of CG, da = the FP64
 // residual); DOT = 2: and sum_cells u' * dc (the z.q of flexible CG).
 // The sweep of one tile by the whole CTA (NW warps); k_tsweep runs it with
@@ -117,9 +161,12 @@ __device__ __forceinline__ void tsweep_tile(const LD<T>& L, const int tile, cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RB = 4;  // rows per warp per batch: their loads are issued together
   const int nz = L.nz;
-  // shared: R[nz][32], two rows for the twist (y_m-1, y_m+1), LO[nz][32]
+  // shared: R[nz][32], spare rows (plain: y_m-1, y_m+1; twisted: y_m-1,
+  // y_m+1, R_m, mu_m, scaled mu_m), LO[nz][32], and for the twisted solve a
+  // third array W[nz][32]: omega / D (FP32) or the scaled multipliers (FP64)
   T* R = reinterpret_cast<T*>(smem_raw);
-  T* LOs = R + (nz + 2) * TW;
+  T* LOs = R + (nz + tsweep_spare_rows(TW2)) * TW;
+  T* Ws = LOs + nz * TW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = tile * TW + lane;
   const bool valid = c < L.nc;
@@ -140,29 +187,36 @@ __device__ __forceinline__ void tsweep_tile(const LD<T>& L, const int tile, cons
     }
   }
   // Small levels (TW2) where one batch of RB rows per warp covers the column
-  // (nz <= RB * NW): phase A also loads w and u~ for phases B' and D, so the
-  // CTA waits for global memory once instead of three times.
+  // (nz <= RB * NW): phase A also loads u~ for phase D, so the CTA waits for
+  // global memory once instead of twice.  (The twisted solve always stages
+  // its third array in shared memory in phase A.)
   const bool carry = TW2 && nz <= RB * NW;
-  T wc[RB], uc_c[RB];
+  T uc_c[RB];
 #pragma unroll
-  for (int i = 0; i < RB; ++i) wc[i] = uc_c[i] = 0;
+  for (int i = 0; i < RB; ++i) uc_c[i] = 0;
+  // FP64 twisted solve: the elimination runs in z = (omega / D) y with the
+  // scaled multipliers, so R is scaled once here and the recurrence is one FMA
+  constexpr bool SC = TW2 && std::is_same<T, double>::value;
+  if (TW2 && warp == 0) {
+    R[(nz + 3) * TW + lane] = valid ? L.mt[c] : (T)0;
+    if (SC) R[(nz + 4) * TW + lane] = valid ? L.mts[c] : (T)0;
+  }
   // A
   for (int l0 = warp; l0 < nz; l0 += RB * NW) {
-    T bl[RB], lo[RB], a0[RB], a1[RB], a2[RB];
+    T bl[RB], lo[RB], a0[RB], a1[RB], a2[RB], wl[RB], ls[RB];
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
       const int l = l0 + i * NW;
-      bl[i] = lo[i] = a0[i] = a1[i] = a2[i] = 0;
+      bl[i] = lo[i] = a0[i] = a1[i] = a2[i] = wl[i] = ls[i] = 0;
       if (valid && l < nz) {
         const int64_t o = (int64_t)l * TW;
         bl[i] = cvt<T>(b[base + o]);
         lo[i] = L.lo[base + o];
-        if (TW2 && carry) {
-          wc[i] = L.w[base + o];
-          if (MODE != MODE_ZERO) {
-            uc_c[i] = u[base + o];
-            if (MODE == MODE_PRO) uc_c[i] += cvt<T>(ec[q + o]);
-          }
+        if (TW2) wl[i] = L.w[base + o];
+        if (SC) ls[i] = L.los[base + o];
+        if (TW2 && carry && MODE != MODE_ZERO) {
+          uc_c[i] = u[base + o];
+          if (MODE == MODE_PRO) uc_c[i] += cvt<T>(ec[q + o]);
         }
         if (MODE != MODE_ZERO) {
           a0[i] = u[s0 + o];
@@ -192,8 +246,13 @@ __device__ __forceinline__ void tsweep_tile(const LD<T>& L, const int tile, cons
         if constexpr (std::is_same<T, float>::value && std::is_same<TB, double>::value) {
           if (bcopy && valid) bcopy[base + (int64_t)l * TW] = (float)bl[i];
         }
+        if (SC) r *= wl[i];
         R[l * TW + lane] = r;
         LOs[l * TW + lane] = lo[i];
+        if (TW2) {
+          Ws[l * TW + lane] = SC ? ls[i] : wl[i];
+          if (l == L.twist) R[(nz + 2) * TW + lane] = r;
+        }
       }
     }
   }
@@ -271,44 +330,37 @@ __device__ __forceinline__ void tsweep_tile(const LD<T>& L, const int tile, cons
     // two chain warps on different sub-partitions, spread over the CTAs
     const int cw0 = tile % NW, cw1 = (cw0 + 1) % NW;
     const int m = L.twist;
-    T* YT = R + nz * TW;   // y_m-1 and y_m+1 kept unscaled for the twist row
+    T* YT = R + nz * TW;    // y_m-1 and y_m+1 for the twist row (FP64: z_m-1, z_m+1)
     T* YB = YT + TW;
-    const T mtv = valid ? L.mt[c] : (T)0;
-    // B
+    const T* RM = YB + TW;  // R_m, kept apart from R[m], which becomes x_m
+    const T* MT = RM + TW;  // mu_m
+    const T* MTS = MT + TW; // mu_m scaled (FP64)
+    // B: elimination, each row stored as z = W y: FP64 eliminates the scaled
+    // R with the scaled multipliers (one FMA a row), FP32 scales y as it goes
     if (warp == cw0) {
-      T y = chain<T>(R, LOs, lane, 0, +1, 0, m, (T)0);
+      T y = SC ? chain<T>(R, Ws, lane, 0, +1, 0, m, (T)0) : chain_scaled<T>(R, LOs, Ws, lane, 0, +1, m, (T)0);
       YT[lane] = y;
     } else if (warp == cw1) {
-      T y = chain<T>(R, LOs, lane, nz - 1, -1, 0, nz - 1 - m, (T)0);
+      T y = SC ? chain<T>(R, Ws, lane, nz - 1, -1, 0, nz - 1 - m, (T)0)
+               : chain_scaled<T>(R, LOs, Ws, lane, nz - 1, -1, nz - 1 - m, (T)0);
       YB[lane] = y;
     }
     __syncthreads();
-    // B'
-    for (int l0 = warp; l0 < nz; l0 += RB * NW) {
-      T wv[RB];
-#pragma unroll
-      for (int i = 0; i < RB; ++i) {
-        const int l = l0 + i * NW;
-        wv[i] = carry ? wc[i] : ((l < nz) ? L.w[base + (int64_t)l * TW] : (T)0);
+    // C: both chain warps complete the twist row,
+    // x_m = (omega / D_m)(R_m - lambda_m y_m-1 - mu_m y_m+1)  (FP64: from z_m-1,
+    // z_m+1 and the scaled multipliers), and substitute outwards
+    if (warp == cw0 || warp == cw1) {
+      const T mtv = MT[lane];
+      const T xm = SC ? fma(-MTS[lane], YB[lane], fma(-Ws[m * TW + lane], YT[lane], RM[lane]))
+                      : Ws[m * TW + lane] * fma(-mtv, YB[lane], fma(-LOs[m * TW + lane], YT[lane], RM[lane]));
+      if (warp == cw0) {
+        R[m * TW + lane] = xm;
+        chain<T>(R, LOs, lane, m - 1, -1, +1, m, xm);
+      } else if (m + 1 < nz) {
+        T x = R[(m + 1) * TW + lane] - mtv * xm;
+        R[(m + 1) * TW + lane] = x;
+        chain<T>(R, LOs, lane, m + 2, +1, -1, nz - 2 - m, x);
       }
-#pragma unroll
-      for (int i = 0; i < RB; ++i) {
-        const int l = l0 + i * NW;
-        if (l < nz) {
-          T y = R[l * TW + lane];
-          if (l == m) y = fma(-mtv, YB[lane], fma(-LOs[m * TW + lane], YT[lane], y));
-          R[l * TW + lane] = y * wv[i];
-        }
-      }
-    }
-    __syncthreads();
-    // C
-    if (warp == cw0) {
-      chain<T>(R, LOs, lane, m - 1, -1, +1, m, R[m * TW + lane]);
-    } else if (warp == cw1 && m + 1 < nz) {
-      T x = R[(m + 1) * TW + lane] - mtv * R[m * TW + lane];
-      R[(m + 1) * TW + lane] = x;
-      chain<T>(R, LOs, lane, m + 2, +1, -1, nz - 2 - m, x);
     }
     __syncthreads();
   }
@@ -1102,7 +1154,7 @@ template <typename T, typename TB, typename TO, int MODE, typename TE, int NW, i
 void tsweep_k(const Level& L, const void* b, const void* u, void* uo, const void* ec, float* bcopy, double omega,
               const SweepDot* dot, cudaStream_t s) {
   auto kern = k_tsweep<T, TB, TO, MODE, TE, NW, DOT, TW2>;
-  size_t smem = (2 * (size_t)L.nz + 2) * TW * sizeof(T);
+  size_t smem = (tsweep_arrays(TW2) * (size_t)L.nz + tsweep_spare_rows(TW2)) * TW * sizeof(T);
   if (DOT && smem < (size_t)DOT * NW * 32 * sizeof(double)) smem = (size_t)DOT * NW * 32 * sizeof(double);
   static SmemOptIn opt_in;
   allow_smem(kern, smem, opt_in);
@@ -1572,7 +1624,8 @@ cudaError_t launch_coarse_cycle(const Level* lv, int ls, int nlev, int nu_pre, i
     a.ub[k] = f32 ? (void*)L.ub32 : (void*)L.ub64;
     a.bb[k] = f32 ? (void*)L.b32 : (void*)L.b64;
     a.ux[k] = f32 ? (void*)L.ux32 : (void*)L.ux64;
-    const size_t sm = (2 * (size_t)L.nz + 2) * TW * (f32 ? sizeof(float) : sizeof(double));
+    const size_t sm = (tsweep_arrays(true) * (size_t)L.nz + tsweep_spare_rows(true)) * TW *
+                      (f32 ? sizeof(float) : sizeof(double));
     if (sm > smem) smem = sm;
   }
   return mixed ? coarse_cycle_launch<true>(a, smem, s) : coarse_cycle_launch<false>(a, smem, s);

@@ -11,6 +11,9 @@
 //   lo, w double[Np]     twisted factorisation N D N^T of H^_z (twist at
 //                        layer `twist`): multipliers and omega / D_l
 //   mt    double[ncp]    the second multiplier of the twist row
+//   los, mts             the same multipliers scaled to the pivot of their
+//                        own row (e/D_l), for the forward recurrence of the
+//                        twisted tile sweep in z = (omega / D) y
 //   *32                  FP32 copies for the mixed-precision cycle (lo32,
 //                        w32, mt32: the factorisation twisted at `twist32`,
 //                        computed in FP64 and rounded once)
@@ -92,6 +95,7 @@ struct Level {
   double4_32a* gh = nullptr;
   float4* gh32 = nullptr;
   double *d = nullptr, *e = nullptr, *lo = nullptr, *w = nullptr, *mt = nullptr;
+  double *los = nullptr, *mts = nullptr;   // Np, ncp: scaled multipliers (FP64 factors)
   float *d32 = nullptr, *e32 = nullptr, *lo32 = nullptr, *w32 = nullptr, *mt32 = nullptr;
   double* theta = nullptr;    // Np
   // cycle work vectors
