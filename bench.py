@@ -71,10 +71,11 @@ FP64_PEAK_TFLOPS = 152 * 4 * 32 / 64 * 2 * 2.07e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 REFERENCE_BUDGET_S = 150.0   # wall time of the --impl reference timed + warm-up steps
 # DRAM bytes per launch of the dominant kernel class of the r6x64 bench (FP64
-# sweeps on the finest level: two plain sweeps and one with the fused r.z per
-# V-cycle), from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
-# of this bench command: 194.9 and 190.5 MB (plain), 193.4 MB (with the dot)
-TRAFFIC_SWEEP_L0_R6X64 = 192.9e6
+# half-column sweeps on the finest level: two plain sweeps and one with the
+# fused r.z per V-cycle), from an ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum of this bench command: 292.8 MB (plain, three
+# launches), 327.8 MB (with the dot)
+TRAFFIC_SWEEP_L0_R6X64 = 304.5e6
 
 
 def measured_peaks():
