@@ -205,8 +205,11 @@ hmg_status hmg_vcycle(hmg_ctx* ctx, int precision, int layout, const void* r,
 hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x,
                      const hmg_solve_params* params, hmg_solve_info* info, void* stream);
 
-/* hmg_solve with HOST buffers: copies b host->device, solves, copies x
- * device->host, all on `stream`; page-locked buffers give asynchronous copies. */
+/* hmg_solve with HOST buffers (b_host, x_host: ncells doubles in the COLUMN
+ * layout), all on `stream`, synchronising before it returns.  Page-locked
+ * buffers that the device can address (cudaHostAlloc'd or registered) are read
+ * and written in place by the layout kernels over the host link; any other
+ * host memory is copied through a device buffer with cudaMemcpyAsync. */
 hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host,
                           const hmg_solve_params* params, hmg_solve_info* info, void* stream);
 

@@ -1802,6 +1802,18 @@ hmg_status hmg_solve(hmg_ctx* ctx, const double* b, double* x, const hmg_solve_p
   return result;
 }
 
+// The device address of page-locked (registered or cudaHostAlloc'd) host
+// memory, or null for any other pointer (pageable host memory, device
+// memory), which the caller then copies.
+static const void* device_address(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host, const hmg_solve_params* params,
                           hmg_solve_info* info, void* stream) {
   if (!ctx) return HMG_ERR_INVALID_ARG;
@@ -1813,11 +1825,24 @@ hmg_status hmg_solve_host(hmg_ctx* ctx, const double* b_host, double* x_host, co
     need_assembled(ctx);
     cudaStream_t s = as_stream(stream);
     Level& L = ctx->lv[0];
-    cuda_ok(cudaMemcpyAsync(ctx->kcol, b_host, (size_t)L.N * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
-    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(L, HMG_FP64, ctx->kcol, ctx->kb, s));
+    // Page-locked host buffers that the device addresses directly are read
+    // and written by the layout kernels over the host link, with no staging
+    // copy; other host memory goes through cudaMemcpyAsync and a device buffer.
+    const void* b_dev = device_address(b_host);
+    void* x_dev = const_cast<void*>(device_address(x_host));
+    if (b_dev) {
+      LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(L, HMG_FP64, b_dev, ctx->kb, s));
+    } else {
+      cuda_ok(cudaMemcpyAsync(ctx->kcol, b_host, (size_t)L.N * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
+      LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_tiled(L, HMG_FP64, ctx->kcol, ctx->kb, s));
+    }
     result = solve_tiled(ctx, *params, info, s);
-    LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_column(L, HMG_FP64, ctx->kx, ctx->kcol, s));
-    cuda_ok(cudaMemcpyAsync(x_host, ctx->kcol, (size_t)L.N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    if (x_dev) {
+      LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_column(L, HMG_FP64, ctx->kx, x_dev, s));
+    } else {
+      LAUNCH(ctx, HMG_K_LAYOUT, 0, s, launch_to_column(L, HMG_FP64, ctx->kx, ctx->kcol, s));
+      cuda_ok(cudaMemcpyAsync(x_host, ctx->kcol, (size_t)L.N * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    }
     cuda_ok(cudaStreamSynchronize(s), "solve");
   });
   if (st != HMG_OK) return st;
