@@ -1094,10 +1094,11 @@ k_tapply(LD<T> L, int ntiles, int RG, const T* __restrict__ x, T* __restrict__ y
 }
 
 constexpr int NW_PAR = 8;
-// Sweep CTA size: 4 warps while a level has more tiles than the GPU has SMs
-// (several CTAs resident per SM keep the FP64 pipes busy, and all CTAs fit in
-// one wave), 16 warps on smaller levels (latency bound: each warp loads only
-// a few rows).
+// Tile-sweep CTA size: 4 warps on levels with more tiles than the GPU has
+// SMs (FP32 levels the register sweep does not cover: several CTAs resident
+// per SM), 16 warps on small levels (latency bound: each warp loads only a
+// few rows), 8 on FP64 levels just above the SM count (one wave).  FP64 levels
+// of more than 160 tiles take the half-column sweep instead.
 constexpr int NW_SWEEP_BIG = 4;
 // FP32 levels up to this many tiles use the staged sweep (k_asweep): there it
 // beats the register-batched one; on larger levels it does not.
