@@ -25,8 +25,10 @@ def _rel(a, b):
     return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
 
+# (6, 8, 3, K): parts of more than 160 tiles take the half-column sweep; with
+# K = 3 the level-1 parts hold 213 and 214 tiles (odd tile counts)
 @pytest.mark.parametrize("r,nz,L,K", [(3, 16, 3, 2), (3, 16, 3, 4), (4, 64, 4, 3), (5, 64, 5, 4), (2, 8, 2, 10),
-                                      (4, 128, 3, 2)])
+                                      (4, 128, 3, 2), (6, 8, 3, 2), (6, 8, 3, 3)])
 def test_partitioned_operator_and_vcycle(r, nz, L, K):
     h = hmg.Hierarchy(r, nz, L)
     h.assemble()
